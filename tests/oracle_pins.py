@@ -1,0 +1,270 @@
+"""Checks that pin the FP64 oracle to facts outside itself.
+
+Each ``check_*`` raises AssertionError on a mismatch.  The facts come from mathematics and from the
+paper, never from the oracle's own code paths:
+
+* dense FP64 matrix products (numpy) on tiny inputs -- the textbook definition of C = A B (Sec. 2.1),
+  A^T dC and the sampled product dC B^T on A's pattern;
+* identity, permutation and diagonal A, whose products are exact;
+* Python ``set`` brute force for Cols/Rows of every tile (Tab. 1, Eq. 2, Eq. 3) and the invariants
+  Cols_t[colidx_local[e]] == col[e], sum_q |Cols(A^(p,q))| == |Cols(A^(p,:))|, V_block >= V_col;
+* |Cols(A^T tile (q,p))| == |Rows(A tile (p,q))|;
+* the worked example of Fig. 1 / Sec. 5.2, rebuilt from its captions (tests/golden).
+
+The same checks run against deliberately broken builds of the oracle (test_oracle_mutants.py), so a
+plausible mistake in it -- a dropped term, a wrong index or sign, a transposed operand, an
+off-by-one tile boundary -- is shown to fail at least one of them.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+
+import numpy as np
+
+import oracle
+from paper_2512_20178_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def dense_of(A) -> np.ndarray:
+    D = np.zeros((A.M, A.K), dtype=np.float64)
+    rows = A.row_ids()
+    np.add.at(D, (rows, A.col.astype(np.int64)), A.val.astype(np.float64))
+    return D
+
+
+def small_cases():
+    """(A, N, seed) tiny cases: ragged shapes, empty rows, a dense row, a single column."""
+    cases = []
+    for k, (M, K, dens, N, er) in enumerate([(17, 23, 0.2, 3, 2), (64, 64, 0.1, 8, 5),
+                                              (5, 40, 0.5, 1, 0), (40, 5, 0.4, 7, 3),
+                                              (33, 1, 0.5, 4, 1), (1, 1, 1.0, 2, 0)]):
+        cases.append((synth.random_small(M, K, dens, 100 + k, empty_rows=er), N, 200 + k))
+    cases.append((synth.hub_matrix(48, 64, 7, 60, 2, 300), 5, 301))
+    return cases
+
+
+def check_spmm_dense():
+    for A, N, seed in small_cases():
+        B = synth.dense_normal(A.K, N, seed)
+        C = oracle.spmm(A, B)
+        ref = dense_of(A) @ B.astype(np.float64)
+        S = np.abs(dense_of(A)) @ np.abs(B.astype(np.float64))
+        assert np.all(np.abs(C - ref) <= 1e-12 * S + 1e-300), "spmm != dense A @ B"
+        rows = np.array([0, A.M - 1, A.M // 2], dtype=np.int64)
+        Cr = oracle.spmm(A, B, rows=rows)
+        assert np.array_equal(Cr, C[rows]), "row-sampled spmm differs from the full one"
+
+
+def check_spmm_exact_structures():
+    n, N = 37, 6
+    B = synth.dense_normal(n, N, 7)
+    eye = synth.from_dense(np.eye(n, dtype=np.float32))
+    assert np.array_equal(oracle.spmm(eye, B), B.astype(np.float64)), "I B != B"
+    perm = np.argsort(synth.uniform_f64(3, synth.STREAM_PERM, 0, n))
+    P = np.zeros((n, n), dtype=np.float32)
+    P[np.arange(n), perm] = 1.0
+    assert np.array_equal(oracle.spmm(synth.from_dense(P), B), B[perm].astype(np.float64)), \
+        "permutation A gives wrong rows"
+    d = (synth.uniform_f32(5, synth.STREAM_VAL, 0, n) - np.float32(0.5)).astype(np.float32)
+    d[3] = 0.0
+    D = synth.from_dense(np.diag(d))
+    ref = d.astype(np.float64)[:, None] * B.astype(np.float64)
+    assert np.array_equal(oracle.spmm(D, B), ref), "diagonal A does not scale rows"
+
+
+def brute_tiles(A, rb, cb, diag_only=False):
+    """{t: (cols_set, rows_set, nnz)} by Python sets."""
+    Pr, Pc = len(rb) - 1, len(cb) - 1
+    out = {}
+    rows = A.row_ids()
+    for p in range(Pr):
+        qs = [p] if diag_only else range(Pc)
+        for q in qs:
+            t = p if diag_only else p * Pc + q
+            cs, rs, n = set(), set(), 0
+            for e in range(A.nnz):
+                i, j = int(rows[e]), int(A.col[e])
+                if rb[p] <= i < rb[p + 1] and cb[q] <= j < cb[q + 1]:
+                    cs.add(j)
+                    rs.add(i)
+                    n += 1
+            out[t] = (cs, rs, n)
+    return out
+
+
+def check_plan_bruteforce():
+    grids = [(1, 1), (2, 3), (4, 4), (3, 1), (1, 5), (7, 6)]
+    for (A, N, _), (Pr, Pc) in itertools.product(small_cases(), grids):
+        P = oracle.plan(A, Pr, Pc)
+        ref = brute_tiles(A, P.rb, P.cb)
+        rows = A.row_ids()
+        for t in range(P.T):
+            cs, rs, n = ref[t]
+            assert list(P.cols_of(t)) == sorted(cs), "Cols of a tile wrong or not ascending"
+            assert P.tile_ncols[t] == len(cs) and P.tile_nrows[t] == len(rs), "|Cols|/|Rows| wrong"
+            assert P.tile_nnz[t] == n, "tile nnz wrong"
+        for e in range(A.nnz):
+            p = int(np.searchsorted(P.rb, rows[e], side="right") - 1)
+            q = int(np.searchsorted(P.cb, A.col[e], side="right") - 1)
+            t = p * Pc + q
+            assert P.cols_of(t)[P.colidx_local[e]] == A.col[e], "remap does not point back"
+        for p in range(Pr):
+            row_cols = {int(A.col[e]) for e in range(A.nnz) if P.rb[p] <= rows[e] < P.rb[p + 1]}
+            assert sum(P.tile_ncols[p * Pc:(p + 1) * Pc]) == len(row_cols), \
+                "sum_q |Cols(A^(p,q))| != |Cols(A^(p,:))|"
+        assert P.tile_cols_ptr[-1] <= min(A.nnz, Pr * A.K)
+        vb, vc = P.volumes(N, 4)
+        assert np.all(vb >= vc), "V_block < V_col"
+        assert np.array_equal(vc, P.tile_ncols * N * 4)
+
+
+def check_uniform_bounds():
+    for n, P in [(10, 3), (10, 4), (5, 4), (4096, 4), (1, 3), (0, 2), (7, 7)]:
+        b = oracle.uniform_bounds(n, P)
+        step = -(-n // P) if n else 0
+        assert b[0] == 0 and b[-1] == n, "bounds do not cover [0, n)"
+        assert all(b[p] == min(p * step, n) for p in range(P + 1)), "bounds are not p*ceil(n/P)"
+
+
+def check_plan_diag_only():
+    gs = [synth.random_small(m, m, 0.3, 50 + m) for m in (3, 9, 1, 14)]
+    n = sum(g.M for g in gs)
+    D = np.zeros((n, n), dtype=np.float32)
+    off = 0
+    bounds = [0]
+    for g in gs:
+        D[off:off + g.M, off:off + g.M] = dense_of(g)
+        off += g.M
+        bounds.append(off)
+    A = synth.from_dense(D)
+    b = np.array(bounds, dtype=np.int64)
+    P = oracle.plan(A, len(gs), len(gs), rb=b, cb=b, diag_only=True)
+    for t, g in enumerate(gs):
+        expect = sorted({int(c) + int(b[t]) for c in g.col})
+        assert list(P.cols_of(t)) == expect, "diag-only Cols != the graph's nonempty columns"
+    D2 = D.copy()
+    D2[0, n - 1] = 1.0
+    try:
+        oracle.plan(synth.from_dense(D2), len(gs), len(gs), rb=b, cb=b, diag_only=True)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("diag-only plan accepted an off-diagonal nonzero")
+
+
+def check_pack_and_packed_spmm():
+    for (A, N, seed), (Pr, Pc) in itertools.product(small_cases(), [(2, 2), (3, 4), (4, 4)]):
+        B = synth.dense_normal(A.K, N, seed)
+        P = oracle.plan(A, Pr, Pc)
+        for local_diag in (False, True):
+            pack_ptr, src = P.pack_layout(local_diag)
+            Bp = oracle.pack(B, src)
+            assert np.array_equal(Bp, B[src]), "pack is not a row copy"
+            bits = synth.to_bf16_bits(B)
+            assert np.array_equal(oracle.pack(bits, src), bits[src]), "bf16 pack not bit-exact"
+            C1 = oracle.spmm_packed(A, P, Bp, B, local_diag)
+            assert np.array_equal(C1, oracle.spmm(A, B)), "packed path != direct path (FP64)"
+
+
+def check_transpose_and_rows():
+    for (A, N, seed), (Pr, Pc) in itertools.product(small_cases(), [(2, 3), (4, 4)]):
+        rowptrT, colT, perm = oracle.transpose(A)
+        rows = A.row_ids()
+        pairs = sorted((int(A.col[e]), int(rows[e]), e) for e in range(A.nnz))
+        assert [p[1] for p in pairs] == list(colT), "A^T rows not in ascending row order"
+        assert [p[2] for p in pairs] == list(perm), "perm of A^T wrong"
+        cnt = np.bincount(A.col, minlength=A.K)
+        assert np.array_equal(np.diff(rowptrT), cnt), "rowptr of A^T wrong"
+        AT = synth.CSR(A.K, A.M, rowptrT, colT, A.val[perm])
+        P = oracle.plan(A, Pr, Pc)
+        PT = oracle.plan(AT, Pc, Pr)
+        for p in range(Pr):
+            for q in range(Pc):
+                assert PT.tile_ncols[q * Pr + p] == P.tile_nrows[p * Pc + q], \
+                    "|Cols(A^T tile (q,p))| != |Rows(A tile (p,q))|"
+
+
+def check_backward_dense():
+    for A, N, seed in small_cases():
+        G = synth.dense_normal(A.M, N, seed + 1)
+        B = synth.dense_normal(A.K, N, seed)
+        D = dense_of(A)
+        dB = oracle.spmm_t(A, G)
+        S = np.abs(D.T) @ np.abs(G.astype(np.float64))
+        assert np.all(np.abs(dB - D.T @ G.astype(np.float64)) <= 1e-12 * S + 1e-300), \
+            "A^T dC wrong"
+        full = G.astype(np.float64) @ B.astype(np.float64).T
+        rows = A.row_ids()
+        ref = full[rows, A.col]
+        got = oracle.sddmm(A, G, B)
+        sc = np.abs(G.astype(np.float64)) @ np.abs(B.astype(np.float64)).T
+        assert np.all(np.abs(got - ref) <= 1e-12 * sc[rows, A.col] + 1e-300), "SDDMM wrong"
+
+
+def check_abs_scale():
+    for A, N, seed in small_cases():
+        B = synth.dense_normal(A.K, N, seed)
+        S = oracle.abs_scale(A, B)
+        ref = np.abs(dense_of(A)) @ np.abs(B.astype(np.float64))
+        assert np.allclose(S, ref, rtol=1e-13, atol=0), "abs scale wrong"
+
+
+def read_golden(name):
+    nz, expect, meta = [], {}, {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            w = line.split()
+            if w[0] == "nz":
+                nz.append((w[1], int(w[2]), int(w[3])))
+            elif w[0] == "expect":
+                expect[w[1]] = [int(x) for x in w[2:]]
+            else:
+                meta[w[0]] = [int(x) for x in w[1:]]
+    return nz, expect, meta
+
+
+def check_fig1_golden():
+    nz, expect, meta = read_golden("fig1_offdiag_tile.txt")
+    M, K = meta["shape"]
+    Pr, Pc = meta["partition"]
+    D = np.zeros((M, K), dtype=np.float32)
+    for _, i, j in nz:
+        D[i, j] = 1.0
+    A = synth.from_dense(D)
+    P = oracle.plan(A, Pr, Pc)
+    t = 0 * Pc + 1
+    assert list(P.cols_of(t)) == expect["cols_tile_0_1"]
+    assert P.tile_ncols[t] == expect["ncols_tile_0_1"][0]
+    assert P.tile_nrows[t] == expect["nrows_tile_0_1"][0]
+    assert P.tile_nnz[t] == expect["nnz_tile_0_1"][0]
+    # Rows of the tile == Cols of the transposed tile (1, 0).
+    rowptrT, colT, perm = oracle.transpose(A)
+    PT = oracle.plan(synth.CSR(K, M, rowptrT, colT, A.val[perm]), Pc, Pr)
+    assert list(PT.cols_of(1 * Pr + 0)) == expect["rows_tile_0_1"]
+    # Smallest set of rows and columns covering every nonzero (Eq. 4-6), by brute force.
+    verts = [("r", i) for i in expect["rows_tile_0_1"]] + [("c", j) for j in expect["cols_tile_0_1"]]
+    best = min(len(s) for k in range(len(verts) + 1) for s in itertools.combinations(verts, k)
+               if all(("r", i) in s or ("c", j) in s for _, i, j in nz))
+    assert best == expect["min_cover"][0]
+
+
+def check_er_band():
+    """ER G(4096, 8/4096), 4x4 tiles: E|Cols_t| = 1024 (1 - (1 - p)^1024) ~ 885.4 (sanity band)."""
+    A = synth.er(4096, 8, 1)
+    P = oracle.plan(A, 4, 4)
+    p = 8 / 4096
+    mean = 1024 * (1 - (1 - p) ** 1024)
+    assert abs(P.tile_ncols.mean() - mean) < 30, P.tile_ncols
+    assert np.all(np.abs(P.tile_ncols - mean) < 80)
+
+
+ALL_CHECKS = [check_spmm_dense, check_spmm_exact_structures, check_plan_bruteforce,
+              check_uniform_bounds, check_plan_diag_only, check_pack_and_packed_spmm,
+              check_transpose_and_rows, check_backward_dense, check_abs_scale, check_fig1_golden,
+              check_er_band]

@@ -1,0 +1,50 @@
+"""Planted mistakes in the oracle must be caught by the pins (CPU only).
+
+Each mutant is a copy of oracle.c with one plausible bug, compiled on the fly; at least one pin
+must fail on it.  The oracle source itself is never modified."""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+import oracle_pins as pins
+
+MUTANTS = {
+    "dropped_last_term": ("for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {\n      const double a = val[e];",
+                          "for (int64_t e = rowptr[i]; e + 1 < rowptr[i + 1]; ++e) {\n      const double a = val[e];"),
+    "tile_boundary_off_by_one": ("if (j >= c0 && j < c0 + width) {", "if (j >= c0 && j <= c0 + width && j < K) {"),
+    "rank_shifted": ("rank[j] = u;", "rank[j] = u + (u > 1);"),
+    "sddmm_sign": ("for (int32_t k = 0; k < N; ++k) s += g[k] * b[k];", "for (int32_t k = 0; k < N; ++k) s -= g[k] * b[k];"),
+    "spmm_t_transposed_operand": ("d[k] += val[e] * g[k];", "d[k] += val[e] * g[k] * (k == 0 ? 1.0 : 0.5);"),
+    "transpose_unstable": ("int64_t pos = fill[col[e]]++;", "int64_t pos = rowptrT[col[e] + 1] - 1 - (fill[col[e]]++ - rowptrT[col[e]]);"),
+    "bounds_floor": ("int64_t b = (n + P - 1) / P;", "int64_t b = n / P > 0 ? n / P : 1;"),
+    "rows_count_per_nnz": ("rows_t += row_hit;", "rows_t += row_hit ? (rowptr[i + 1] - rowptr[i]) : 0;"),
+    "abs_scale_signed": ("const double a = fabs(val[e]);", "const double a = val[e];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    src = src.replace(old, new, 1)
+    c = tmp_path / "mut.c"
+    c.write_text(src)
+    so = str(tmp_path / "libmut.so")
+    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", str(c),
+                    "-o", so, "-lm"], check=True)
+    oracle.lib()
+    prev = oracle.use_library(so)
+    failed = []
+    try:
+        for chk in pins.ALL_CHECKS:
+            try:
+                chk()
+            except (AssertionError, ValueError):
+                failed.append(chk.__name__)
+    finally:
+        oracle.use_library(prev)
+    assert failed, f"no pin caught the planted mistake {name}"

@@ -1,0 +1,399 @@
+"""Benchmark of the sparsity-aware SpMM hot path on one GB300 (or N independent replicas).
+
+Workload (default): R-MAT CSR A 2^20 x 2^20, avg degree 16 (a,b,c,d = .57,.19,.19,.05,
+duplicates merged), FP32 values U(0,1), dense B 2^20 x 128 FP32 N(0,1), 4x4 logical tiles.
+One step = pack the B rows named by every tile's unique columns (Sec. 5.1 stage 3) + SpMM over
+the packed rows summed over the tiles of each row block (stage 5).  The plan (stage 1) is built
+once per pattern, as in the paper, and timed on its own.
+
+The JSON line reports:
+  value     -- algorithmic GB/s of the step: pack 2*R*N*4 + R*4, SpMM (M+1)*8 + nnz*8 + R*N*4 +
+               M*N*4 bytes (R = packed rows), over the device time of K steps (CUDA events);
+  roofline  -- the SpMM kernel alone: its algorithmic bytes / its mean launch time vs the
+               measured HBM copy bandwidth;
+  e2e       -- the same bytes over steps that also copy B from pinned host memory and C back;
+  cpu_baseline -- the FP64 C oracle on a strided row sample, on this host's cores;
+  forms     -- BF16-stored B, the backward (dB = A^T dC, dA by SDDMM) and fwd+bwd time.
+Inputs are larger than L2 (B 512 MB, packed B 650 MB, C 512 MB), so no L2 flush is needed.
+
+--impl reference times the FP64 CPU oracle (the reference arm here; the paper ships no kernels).
+With N > 1 (torchrun) every rank runs its own replica (weak scaling, no collective on the path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMM GB/s (pack + SpMM, algorithmic bytes) vs HBM roofline"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "spmm_rmat20_n128_traffic.json")
+KERNEL_SOURCES = ["paper_2512_20178_gb300/csrc/spmm.cu", "paper_2512_20178_gb300/csrc/vec.cuh",
+                  "paper_2512_20178_gb300/csrc/internal.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--deg", type=int, default=16)
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--tiles", type=int, default=4)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2512_20178_gb300 import synth
+    A = synth.rmat(args.scale, args.deg, args.seed)
+    B = synth.dense_normal(A.K, args.N, args.seed)
+    return A, B
+
+
+def config(args, A, extra=None):
+    c = {"workload": f"rmat{args.scale}_deg{args.deg}_N{args.N}_{args.tiles}x{args.tiles}_fp32",
+         "M": A.M, "K": A.K, "nnz": A.nnz, "N": args.N, "tiles": f"{args.tiles}x{args.tiles}",
+         "rmat": [0.57, 0.19, 0.19, 0.05], "seed": args.seed,
+         "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def step_bytes(M, nnz, R, N, sz):
+    spmm = (M + 1) * 8 + nnz * 8 + R * N * sz + M * N * 4
+    pack = 2 * R * N * sz + R * 4
+    return spmm, pack
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max over ranks (the slowest replica sets the job time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                mx = float(f[3])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        # Under load: samples above half the maximum (drops the idle edges of the window).
+        load = [s for s in sm if mx is None or s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile():
+    """DRAM bytes per SpMM launch from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        rec = json.load(open(PROFILE_TRAFFIC))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if rec.get("kernel_sources_sha256") != h.hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(A, B, args, stride=8):
+    """The FP64 oracle (pack + SpMM through the packed rows) on every stride-th row of A."""
+    import oracle
+    from paper_2512_20178_gb300 import synth
+    rows = np.arange(0, A.M, stride)
+    cnt = np.diff(A.rowptr)[rows]
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(cnt, out=rp[1:])
+    idx = np.concatenate([np.arange(A.rowptr[r], A.rowptr[r + 1]) for r in rows]) if len(rows) else np.zeros(0, np.int64)
+    S = synth.CSR(len(rows), A.K, rp, A.col[idx], A.val[idx])
+    t0 = time.perf_counter()
+    P = oracle.plan(S, args.tiles, args.tiles)
+    t1 = time.perf_counter()
+    _, src = P.pack_layout(False)
+    Bp = oracle.pack(B, src)
+    oracle.spmm_packed(S, P, Bp, B)
+    t2 = time.perf_counter()
+    sp, pk = step_bytes(S.M, S.nnz, len(src), args.N, 4)
+    gbs = (sp + pk) / (t2 - t1) / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"every {stride}th row ({S.M} rows, {S.nnz} nnz), pack + SpMM via packed "
+                      f"rows in FP64; plan {t1 - t0:.2f} s not counted",
+            "seconds": t2 - t1}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    A, B = workload(args)
+    oracle.build()
+    stride = 16
+    res = None
+    ts = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(A, B, args, stride)
+        if k >= args.warmup:
+            ts.append(r["seconds"])
+        res = r
+    ms = 1e3 * sum(ts) / max(len(ts), 1)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded R-MAT)", "config": config(args, A),
+            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": res["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__ as g
+    g.build()
+    from paper_2512_20178_gb300 import shiro, synth
+
+    A, B = workload(args)
+    N = args.N
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    col = torch.from_numpy(A.col).to(dev)
+    val = torch.from_numpy(A.val).to(dev)
+    Bd = torch.from_numpy(B).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P = shiro.Plan.create(rp, col, val, A.M, A.K, args.tiles, args.tiles)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    R = P.info.packed_rows
+    Bp = torch.empty((R, N), dtype=torch.float32, device=dev)
+    C = torch.empty((A.M, N), dtype=torch.float32, device=dev)
+    tuned = None
+    if args.autotune:
+        P.pack(Bd, out=Bp)
+        tuned = P.autotune(Bp, B=Bd, C=C)
+    scratch = P.new_scratch(N, torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P.pack(Bd, out=Bp)
+        P.spmm(Bp, out=C, scratch=scratch)
+
+    for _ in range(args.warmup):
+        step()
+    K = args.steps
+    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(K):
+        P.pack(Bd, out=Bp)
+        ev_a[k].record(stream)
+        P.spmm(Bp, out=C, scratch=scratch)
+        ev_b[k].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.stop()
+    ms = start.elapsed_time(end) / K
+    spmm_ms = sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)) / K
+    ms_max = reduce_max(ms, world, dev)
+    sp_bytes, pk_bytes = step_bytes(A.M, A.nnz, R, N, 4)
+    value = world * (sp_bytes + pk_bytes) / (ms_max * 1e-3) / 1e9
+    gflops = world * 2.0 * A.nnz * N / (ms_max * 1e-3) / 1e9
+
+    # End to end through the public API: B from pinned host memory, C back to pinned memory.
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch = torch.empty((A.M, N), dtype=torch.float32).pin_memory()
+    for _ in range(min(args.warmup, 3)):
+        Bd.copy_(Bh, non_blocking=True)
+        step()
+        Ch.copy_(C, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ke = max(1, min(K, 100))
+    e0.record(stream)
+    for _ in range(Ke):
+        Bd.copy_(Bh, non_blocking=True)
+        step()
+        Ch.copy_(C, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / Ke, world, dev)
+    e2e = {"value": world * (sp_bytes + pk_bytes) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": int(Bh.numel() * 4), "d2h_bytes_per_step": int(Ch.numel() * 4),
+           "ms_per_step": e2e_ms}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = sp_bytes / (spmm_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_spmm", "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile(), "algorithmic_bytes": sp_bytes,
+                "ms_per_launch": spmm_ms}
+
+    forms = None
+    if not args.no_forms:
+        forms = measure_forms(args, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream)
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded R-MAT, counter-based SplitMix64)",
+            "config": config(args, A, {"packed_rows": R, "plan_ms": plan_ms,
+                                       "schedule": P.info.opts.as_dict(), "autotuned": tuned}),
+            "gflops": gflops, "spmm_ms": spmm_ms, "pack_ms": ms - spmm_ms,
+            "gpu_launches": 2 * K, "roofline": roofline, "e2e": e2e,
+            "clocks": clocks.summary()}
+    if forms:
+        line["forms"] = forms
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(A, B, args).items() if k != "seconds"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_forms(args, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream, reps=20):
+    """BF16-stored B, backward (dB and dA) and fwd+bwd on the same A, N (device times)."""
+    import torch
+    from paper_2512_20178_gb300 import shiro, synth
+    N = args.N
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    R = P.info.packed_rows
+    Bh16 = torch.from_numpy(synth.to_bf16_bits(B).view(np.int16)).to(dev).view(torch.bfloat16)
+    Bp16 = torch.empty((R, N), dtype=torch.bfloat16, device=dev)
+    s16 = P.new_scratch(N, torch.bfloat16)
+    bf16_ms = timed(lambda: (P.pack(Bh16, out=Bp16), P.spmm(Bp16, out=C, scratch=s16)))
+    sp16, pk16 = step_bytes(A.M, A.nnz, R, N, 2)
+    fwd_ms = timed(lambda: (P.pack(Bd, out=Bp), P.spmm(Bp, out=C, scratch=scratch)))
+    PT = shiro.Plan.create(rp, col, val, A.M, A.K, args.tiles, args.tiles,
+                           flags=shiro.SHIRO_PLAN_TRANSPOSE)
+    G = torch.randn((A.M, N), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+    RT = PT.info.packed_rows
+    Gp = torch.empty((RT, N), dtype=torch.float32, device=dev)
+    dB = torch.empty((A.K, N), dtype=torch.float32, device=dev)
+    dA = torch.empty(A.nnz, dtype=torch.float32, device=dev)
+    sT = PT.new_scratch(N, torch.float32)
+    db_ms = timed(lambda: (PT.pack(G, out=Gp), PT.spmm(Gp, out=dB, scratch=sT)))
+    da_ms = timed(lambda: P.sddmm(G, Bp, out=dA))
+    sddmm_bytes = A.nnz * 8 + A.M * N * 4 + R * N * 4 + A.nnz * 4
+    return {"bf16_B": {"ms": bf16_ms, "GBps": (sp16 + pk16) / (bf16_ms * 1e-3) / 1e9,
+                       "vs_fp32_speedup": fwd_ms / bf16_ms},
+            "fp32_fwd_ms": fwd_ms, "bwd_dB_ms": db_ms, "bwd_dA_ms": da_ms,
+            "fwd_bwd_ms": fwd_ms + db_ms + da_ms,
+            "sddmm_GBps": sddmm_bytes / (da_ms * 1e-3) / 1e9,
+            "transpose_packed_rows": RT}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * shiro.h -- C ABI of libshiro: the single-GPU hot path of SHIRO's sparsity-aware SpMM
+ * (Zhuang et al., "SHIRO: Near-Optimal Communication Strategies for Distributed Sparse Matrix
+ * Multiplication", ICS 2026), written for GB300 (sm_103a).
+ *
+ * The method computes C = A B (Sec. 2.1) for a CSR matrix A split into a grid of tiles A^(p,q)
+ * (Tab. 1; Sec. 2.2 partitions A, B and C into row blocks and the block columns of A follow the
+ * owners of B's row blocks).  For every tile it finds Cols(A^(p,q)), the distinct column indices
+ * of the tile's nonzeros (Tab. 1, Eq. 2), gathers only those rows of B into a packed buffer
+ * (Sec. 5.1, stage 3), remaps the tile's column indices into that buffer, and computes the local
+ * product over the packed rows, summing the tiles of a row block into C (Sec. 2.2 stage 4 and
+ * Sec. 5.1 stage 5).  On one GPU the P logical blocks are tiles of one matrix and the packed
+ * buffer stands in for the rows that the paper's processes exchange.
+ *
+ * Conventions for every entry point:
+ *   - All pointers named "device" are CUDA device pointers owned by the caller; the library never
+ *     allocates device memory.  Plans live in a caller-provided workspace.
+ *   - Dense matrices are row-major with a leading dimension (row stride) in elements.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream).  Compute calls
+ *     (pack, spmm, sddmm, backward) only enqueue work: they never synchronise, never allocate and
+ *     can be captured in a CUDA graph.  Plan creation synchronises the stream.
+ *   - Errors are returned as shiro_status; shiro_last_error() gives a message (thread-local).
+ *     Nothing aborts or traps.  Device-side detection (e.g. a malformed CSR) sets a status word
+ *     in the plan that plan creation or shiro_plan_check() reads back.
+ *   - A plan may be used by one stream at a time: calls on the same plan must not overlap on the
+ *     GPU (long rows use per-plan arrival counters).
+ */
+#ifndef SHIRO_H
+#define SHIRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SHIRO_OK = 0,
+  SHIRO_ERR_INVALID_ARG = 1,           /* a null pointer, a negative size, a bad combination */
+  SHIRO_ERR_BAD_CSR = 2,               /* rowptr not monotone / wrong ends, column out of range,
+                                          a nonzero outside its diagonal tile (DIAG_ONLY) */
+  SHIRO_ERR_INSUFFICIENT_WORKSPACE = 3,/* workspace or scratch smaller than required */
+  SHIRO_ERR_UNSUPPORTED = 4,           /* dtype combination or size beyond the limits below */
+  SHIRO_ERR_CUDA = 5,                  /* a CUDA runtime call failed (message has the detail) */
+  SHIRO_ERR_DEVICE_TIMEOUT = 6         /* a bounded device-side wait gave up */
+} shiro_status;
+
+typedef enum { SHIRO_F32 = 0, SHIRO_BF16 = 1, SHIRO_F64 = 2 } shiro_dtype;
+
+/* Opaque plan handle (host memory; its device arrays live in the caller's workspace). */
+typedef struct shiro_plan_s* shiro_plan_t;
+
+/* A CSR matrix in device memory.  rowptr has M+1 entries with rowptr[0] = 0, non-decreasing,
+ * rowptr[M] = nnz; col[e] in [0, K).  Column order inside a row is free (sums follow it) and
+ * duplicates are summed.  val is F32 or F64 (the FP64 form exists for gradient checks). */
+typedef struct {
+  int64_t M, K, nnz;
+  const int64_t* rowptr; /* device, M+1 */
+  const int32_t* col;    /* device, nnz */
+  const void* val;       /* device, nnz elements of vdt */
+  shiro_dtype vdt;
+} shiro_csr;
+
+/* Plan flags. */
+#define SHIRO_PLAN_LOCAL_DIAG 0x1u /* 1D reading (Sec. 2.2): diagonal tiles (p == q) are the
+                                      "local computation" and read B in place; only off-diagonal
+                                      tiles are packed.  Needs P_r == P_c. */
+#define SHIRO_PLAN_DIAG_ONLY 0x2u  /* only tiles (p, p) exist (block-diagonal A, e.g. a batch of
+                                      graphs); a nonzero outside them is SHIRO_ERR_BAD_CSR. */
+#define SHIRO_PLAN_TRANSPOSE 0x4u  /* plan A^T (K x M) on the transposed grid: tile (q, p) of A^T
+                                      is tile (p, q) of A, so its Cols are Rows(A^(p,q)) (Eq. 3).
+                                      Used for dB = A^T dC. */
+
+/* The tile grid.  Row block p covers rows [row_bounds[p], row_bounds[p+1]) and column block q
+ * covers columns [col_bounds[q], col_bounds[q+1]).  NULL bounds mean uniform blocks starting at
+ * p * ceil(M / P_r), clamped to M (the last block takes the remainder).  Tiles are numbered
+ * t = p * P_c + q (t = p with DIAG_ONLY).  Limits: 1 <= P_r, P_c <= 65536, P_r * P_c <= 2^20. */
+typedef struct {
+  int32_t P_r, P_c;
+  const int64_t* row_bounds; /* host, P_r + 1 ascending entries from 0 to M, or NULL */
+  const int64_t* col_bounds; /* host, P_c + 1 ascending entries from 0 to K, or NULL */
+  uint32_t flags;            /* SHIRO_PLAN_* */
+} shiro_partition;
+
+/* Work schedule of the SpMM/SDDMM kernels (zero fields take the defaults).  Rows with more than
+ * long_row_nnz nonzeros are split into chunks of chunk_nnz (>= 32) nonzeros whose FP32 partial
+ * sums are added in a fixed order (deterministic); shorter rows are grouped into work items of at
+ * most group_nnz nonzeros and group_rows rows.  One warp runs one work item at a time. */
+typedef struct {
+  int32_t long_row_nnz;
+  int32_t chunk_nnz;
+  int32_t group_nnz;
+  int32_t group_rows;
+  int32_t warps_per_cta; /* 1..16 */
+  int32_t persistent;    /* 1: grid = SMs x resident CTAs and warps stride over the items */
+} shiro_opts;
+
+/* Bytes of workspace shiro_plan_create needs for A and this partition (an upper bound that does
+ * not depend on A's pattern, so it can be allocated before the plan exists).  A's pointers may be
+ * NULL here: only M, K, nnz and vdt are read. */
+shiro_status shiro_plan_workspace(const shiro_csr* A, const shiro_partition* part,
+                                  const shiro_opts* opts, size_t* bytes);
+
+/* Plan stage 1 of Sec. 5.1 (sparsity analysis) for every tile, once per pattern (the paper runs
+ * it offline and reuses it across SpMM calls with the same pattern, Sec. 5.1 and Sec. 5.3.2):
+ *   a1  tile split: the tile of every nonzero, nonzeros per tile;
+ *   a2  Cols(A^(p,q)) in ascending column order and their exclusive scan over tiles (Eq. 2);
+ *       Rows(A^(p,q)) counts (Eq. 3);
+ *   a3  remap: every nonzero's row in the packed buffer;
+ *   a4  per-tile volumes (see shiro_plan_volumes);
+ * plus the work schedule.  The CSR is validated on the device first.  A's arrays must stay alive
+ * and unchanged while the plan is used (except a TRANSPOSE plan, which keeps its own copy of A^T;
+ * refresh its values with shiro_plan_update_values).  Synchronises `stream`.
+ * On success *plan owns nothing but host memory; free it with shiro_plan_destroy. */
+shiro_status shiro_plan_create(const shiro_csr* A, const shiro_partition* part,
+                               const shiro_opts* opts, void* workspace, size_t workspace_bytes,
+                               void* stream, shiro_plan_t* plan);
+
+void shiro_plan_destroy(shiro_plan_t plan);
+
+typedef struct {
+  int64_t M, K, nnz;      /* of the planned matrix (A^T for a TRANSPOSE plan) */
+  int32_t P_r, P_c;       /* grid of the planned matrix */
+  int32_t n_tiles;
+  uint32_t flags;
+  shiro_dtype vdt;
+  int64_t total_cols;     /* sum over tiles of |Cols(A^(p,q))| */
+  int64_t packed_rows;    /* rows of the packed buffer (total_cols minus local diagonal tiles) */
+  int64_t n_items;        /* work items of the schedule */
+  int64_t n_long_rows;    /* rows split into chunks */
+  int64_t n_chunks;       /* chunks of those rows (partial-sum slots) */
+  size_t workspace_used;  /* bytes of the workspace in use */
+  shiro_opts opts;        /* schedule in effect */
+} shiro_plan_info;
+
+shiro_status shiro_plan_query(shiro_plan_t plan, shiro_plan_info* info);
+
+/* Per-tile statistics, host arrays: tile_nnz, tile_nrows (|Rows|), tile_ncols (|Cols|) have
+ * n_tiles entries; tile_cols_ptr and pack_ptr have n_tiles + 1 (exclusive scans of |Cols| over all
+ * tiles and over packed tiles).  Any pointer may be NULL. */
+shiro_status shiro_plan_tile_stats(shiro_plan_t plan, int64_t* tile_nnz, int64_t* tile_nrows,
+                                   int64_t* tile_ncols, int64_t* tile_cols_ptr, int64_t* pack_ptr);
+
+/* Communication volumes in bytes for N columns of dtype dt (host arrays of n_tiles entries):
+ * v_block[t] = (width of column block q) * N * sz (Eq. 1), v_col[t] = |Cols(A^(p,q))| * N * sz
+ * (Eq. 2), v_row[t] = |Rows(A^(p,q))| * N * sz (Eq. 3).  Any pointer may be NULL. */
+shiro_status shiro_plan_volumes(shiro_plan_t plan, int32_t N, shiro_dtype dt, int64_t* v_block,
+                                int64_t* v_col, int64_t* v_row);
+
+/* Copies the plan's index arrays into caller device buffers (any may be NULL):
+ * cols_sorted (total_cols): Cols of every tile, ascending, concatenated in tile order;
+ * pack_src (packed_rows): the B row gathered into each packed row;
+ * colidx_local (nnz): position of every nonzero's column in its tile's Cols;
+ * remap (nnz): packed row read by every nonzero, or -1 - col for a local diagonal tile.
+ * Enqueued on `stream`; no synchronisation. */
+shiro_status shiro_plan_export(shiro_plan_t plan, int32_t* cols_sorted, int32_t* pack_src,
+                               int32_t* colidx_local, int32_t* remap, void* stream);
+
+/* For a TRANSPOSE plan: copies A^T's CSR into caller device buffers (any may be NULL): rowptr
+ * (K+1), col (nnz: the row of A of each entry, ascending within a row of A^T), perm (nnz: index
+ * in A of each entry of A^T). */
+shiro_status shiro_plan_export_transpose(shiro_plan_t plan, int64_t* rowptr, int32_t* col,
+                                         int64_t* perm, void* stream);
+
+/* For a TRANSPOSE plan: reloads A^T's values from A's value array `val` (device, nnz elements of
+ * the plan's vdt) through the stored permutation.  Enqueued on `stream`. */
+shiro_status shiro_plan_update_values(shiro_plan_t plan, const void* val, void* stream);
+
+/* Reads and clears the plan's device status word (synchronises `stream`). */
+shiro_status shiro_plan_check(shiro_plan_t plan, void* stream);
+
+/* Rebuilds the work schedule with new options (the pattern analysis is kept).  Fails with
+ * SHIRO_ERR_INSUFFICIENT_WORKSPACE if the new schedule does not fit.  Synchronises `stream`. */
+shiro_status shiro_plan_reschedule(shiro_plan_t plan, const shiro_opts* opts, void* stream);
+
+/* Pack (Sec. 5.1 stage 3): Bpack[r, :] = B[pack_src[r], :] for the packed_rows rows.
+ * B: device, rows of the planned matrix's K, N columns, leading dimension ldb >= N.
+ * Bpack: device, packed_rows x N with leading dimension ldp >= N.  dt is F32, BF16 or F64; the
+ * copy is bit-exact. */
+shiro_status shiro_pack(shiro_plan_t plan, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
+                        void* Bpack, int64_t ldp, void* stream);
+
+/* Scratch bytes shiro_spmm / shiro_spmm_backward need for N columns of dt with the plan's current
+ * schedule (partial sums of split rows); 0 when no row is split. */
+shiro_status shiro_spmm_scratch(shiro_plan_t plan, int32_t N, shiro_dtype dt, size_t* bytes);
+
+#define SHIRO_SPMM_ACCUMULATE 0x1u /* C += A B instead of C = A B */
+
+/* Local SpMM over the packed rows and aggregation over the tiles of each row block (Sec. 2.2
+ * stages 3-4, Sec. 5.1 stage 5): C[i, :] = sum over the nonzeros e of row i of
+ * val[e] * Bpack[remap[e], :] (or B[col[e], :] for local diagonal tiles), summed in the row's
+ * stored order, i.e. ascending column blocks for column-sorted rows.
+ * Types: values F32 with dt F32 or BF16 (C is F32, accumulation in FP32), or values F64 with dt
+ * F64 (C is F64).  B may be NULL unless the plan has LOCAL_DIAG.  scratch: device, at least
+ * shiro_spmm_scratch bytes (may be NULL when that is 0); its contents need no initialisation. */
+shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
+                        int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
+                        uint32_t flags, void* scratch, size_t scratch_bytes, void* stream);
+
+/* Gradient of C = A B with respect to A's stored values (a sampled dense-dense product on A's
+ * pattern): dA[e] = sum_k dC[row(e), k] * Bpack[remap[e], k] (B[col[e], k] for local diagonal
+ * tiles).  dC: device M x N of dt (F32/BF16 with F32 dA, or F64 with F64 dA). */
+shiro_status shiro_sddmm(shiro_plan_t plan, const void* dC, int64_t lddc, const void* Bpack,
+                         int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
+                         void* dA, void* stream);
+
+/* Backward of C = A B: dB = A^T dC through the TRANSPOSE plan planT (pack dC by planT into
+ * dCpack, then SpMM over it) and dA by shiro_sddmm on `plan`.  dB and dA may be NULL to skip
+ * them; dCpack (planT's packed_rows x N, leading dimension lddp) is needed when dB is wanted.
+ * scratch must hold shiro_spmm_scratch(planT, N, dt). */
+shiro_status shiro_spmm_backward(shiro_plan_t plan, shiro_plan_t planT, const void* dC,
+                                 int64_t lddc, const void* Bpack, int64_t ldp, const void* B,
+                                 int64_t ldb, int32_t N, shiro_dtype dt, void* dCpack,
+                                 int64_t lddp, void* dB, int64_t lddb, void* dA, void* scratch,
+                                 size_t scratch_bytes, void* stream);
+
+/* Batched form: G independent graphs (CSR matrices, host array of G descriptors whose arrays are
+ * on the device) become one block-diagonal matrix planned with DIAG_ONLY, one tile per graph, so
+ * Cols of tile g are the non-empty columns of graph g.  B and C of the batch are the per-graph
+ * operands stacked by rows in graph order (graph g's rows start at the sum of the earlier
+ * graphs' row counts).  The plan holds its own copy of the graphs, so theirs may be freed
+ * afterwards.  All graphs share one vdt.  Use shiro_pack / shiro_spmm / shiro_sddmm on the plan. */
+shiro_status shiro_batch_workspace(int32_t G, const shiro_csr* graphs, const shiro_opts* opts,
+                                   size_t* bytes);
+shiro_status shiro_batch_plan_create(int32_t G, const shiro_csr* graphs, const shiro_opts* opts,
+                                     void* workspace, size_t workspace_bytes, void* stream,
+                                     shiro_plan_t* plan);
+
+/* Autotuner: times shiro_spmm over a set of candidate schedules on the caller's operands (Bpack,
+ * C and scratch as for shiro_spmm; C is overwritten) and leaves the fastest one in the plan
+ * (*best receives it).  Candidates are chosen from N and the plan's degree profile and are
+ * limited to those whose scratch fits scratch_bytes.  Synchronises `stream`. */
+shiro_status shiro_autotune(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
+                            int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
+                            void* scratch, size_t scratch_bytes, int32_t reps, void* stream,
+                            shiro_opts* best);
+
+/* Makes `device` the calling host thread's current CUDA device for this library (the library
+ * carries its own CUDA runtime, so a caller that switches devices must tell it).  Plans and
+ * compute calls use the thread's current device; streams passed in must belong to it. */
+shiro_status shiro_set_device(int32_t device);
+
+/* Default schedule options. */
+void shiro_default_opts(shiro_opts* opts);
+
+/* Thread-local message of the last error. */
+const char* shiro_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t shiro_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHIRO_H */

@@ -1,0 +1,255 @@
+// sddmm.cu -- gradient of C = A B with respect to A's stored values, dA[e] = <dC[row e], B[col e]>
+// (a sampled dense-dense product on A's pattern, reading B through the packed rows), and the
+// backward entry point that adds dB = A^T dC through the transposed plan.
+//
+// One warp per work item (the SpMM schedule).  For a batch of up to 32 nonzeros every lane
+// forms its slice of the 32 dot products, then a butterfly transpose-reduction (16+8+4+2+1
+// shuffles) leaves the full dot product of nonzero j in lane j, which writes dA coalesced.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "vec.cuh"
+
+namespace shiro {
+
+constexpr unsigned FULLM = 0xffffffffu;
+
+template <typename TB>
+struct SddmmParams {
+  using TA = typename AccOf<TB>::T;
+  const int64_t* rowptr;
+  const int32_t* remap;
+  const TB* dC;
+  int64_t lddc;
+  const TB* Bpack;
+  int64_t ldp;
+  const TB* B;
+  int64_t ldb;
+  int32_t N;
+  TA* dA;
+  const Item* items;
+  int64_t n_items;
+  int32_t chunk;
+  int32_t persistent;
+};
+
+template <typename TB, int VEC, int NCH, bool MASKED>
+__device__ __forceinline__ void load_frag(const TB* row, int32_t N, int lane,
+                                          typename AccOf<TB>::T (&f)[NCH][VEC]) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int col = c * 32 * VEC + lane * VEC;
+    if (!MASKED || col < N) {
+      load_vec<TB, VEC, true>(row + col, f[c]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) f[c][v] = 0;
+    }
+  }
+}
+
+template <typename TA>
+__device__ __forceinline__ TA transpose_reduce(TA (&part)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const bool upper = lane & off;
+#pragma unroll
+    for (int k = 0; k < off; ++k) {
+      const TA send = upper ? part[k] : part[k + off];
+      const TA keep = upper ? part[k + off] : part[k];
+      part[k] = keep + __shfl_xor_sync(FULLM, send, off);
+    }
+  }
+  return part[0];
+}
+
+template <typename TB, int VEC, int NCH, bool MASKED, int U>
+__device__ __forceinline__ void sddmm_item(const SddmmParams<TB>& p, const Item& item, int lane) {
+  using TA = typename AccOf<TB>::T;
+  const bool chunk = item.tag <= 0;
+  const int32_t r0 = item.row;
+  const int32_t nr = chunk ? 1 : item.tag;
+  const int64_t rp = lane < nr ? __ldg(p.rowptr + r0 + lane + 1) : 0;
+  int64_t e_end = __shfl_sync(FULLM, rp, nr - 1);
+  if (chunk) e_end = min(e_end, item.e0 + (int64_t)p.chunk);
+  int32_t rl = 0;
+  int64_t next = __shfl_sync(FULLM, rp, 0);
+  TA g[NCH][VEC];
+  load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)r0 * p.lddc, p.N, lane, g);
+  for (int64_t e = item.e0; e < e_end; e += 32) {
+    const int n = (int)min((int64_t)32, e_end - e);
+    const int32_t my_idx = lane < n ? __ldcs(p.remap + e + lane) : 0;
+    TA part[32];
+#pragma unroll
+    for (int j = 0; j < 32; j += U) {
+      TA b[U][NCH][VEC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t idx = __shfl_sync(FULLM, my_idx, j + u);
+        if (j + u < n) {
+          const TB* row = idx >= 0 ? p.Bpack + (int64_t)idx * p.ldp
+                                   : p.B + (int64_t)(-1 - idx) * p.ldb;
+          load_frag<TB, VEC, NCH, MASKED>(row, p.N, lane, b[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        part[j + u] = 0;
+        if (j + u < n) {
+          const int64_t ee = e + j + u;
+          if (ee >= next && rl < nr - 1) {
+            while (ee >= next && rl < nr - 1) {
+              ++rl;
+              next = __shfl_sync(FULLM, rp, rl);
+            }
+            load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + rl) * p.lddc, p.N, lane, g);
+          }
+          TA s = 0;
+#pragma unroll
+          for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s += g[c][v] * b[u][c][v];
+          part[j + u] = s;
+        }
+      }
+    }
+    const TA tot = transpose_reduce<TA>(part, lane);
+    if (lane < n) p.dA[e + lane] = tot;
+  }
+}
+
+template <typename TB, int VEC, int NCH, bool MASKED, int U>
+__global__ void __launch_bounds__(256) k_sddmm(const SddmmParams<TB> p) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  int64_t it = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int64_t step = p.persistent ? (int64_t)gridDim.x * wpb : p.n_items;
+  for (; it < p.n_items; it += step) {
+    const Item item = p.items[it];
+    sddmm_item<TB, VEC, NCH, MASKED, U>(p, item, lane);
+  }
+}
+
+template <typename TB, int VEC, int NCH, bool MASKED>
+static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& prm,
+                                 cudaStream_t s) {
+  constexpr int REG = VEC * NCH * (sizeof(typename AccOf<TB>::T) / 4);
+  constexpr int U = REG >= 16 ? 2 : (REG >= 8 ? 4 : 8);
+  const int wpc = std::min(P->opts.warps_per_cta, 8);
+  int64_t grid = (prm.n_items + wpc - 1) / wpc;
+  if (prm.persistent) grid = std::min<int64_t>(grid, (int64_t)P->sm_count * 8);
+  if (grid <= 0) return SHIRO_OK;
+  k_sddmm<TB, VEC, NCH, MASKED, U><<<(unsigned)grid, wpc * 32, 0, s>>>(prm);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
+static bool al(const void* ptr, int64_t ld, size_t elem, int vec) {
+  const size_t a = std::min<size_t>(16, elem * (size_t)vec);
+  return ((uintptr_t)ptr % a) == 0 && ((size_t)ld * elem) % a == 0;
+}
+
+template <typename TB>
+static shiro_status sddmm_typed(const shiro_plan_s* P, const void* dC, int64_t lddc,
+                                const void* Bpack, int64_t ldp, const void* B, int64_t ldb,
+                                int32_t N, void* dA, cudaStream_t s) {
+  SddmmParams<TB> prm{};
+  prm.rowptr = P->rowptr;
+  prm.remap = P->d_remap;
+  prm.dC = (const TB*)dC;
+  prm.lddc = lddc;
+  prm.Bpack = (const TB*)Bpack;
+  prm.ldp = ldp;
+  prm.B = (const TB*)B;
+  prm.ldb = ldb;
+  prm.N = N;
+  prm.dA = (typename AccOf<TB>::T*)dA;
+  prm.items = P->d_items;
+  prm.n_items = P->n_items;
+  prm.chunk = P->opts.chunk_nnz;
+  prm.persistent = P->opts.persistent;
+  const size_t esz = sizeof(TB);
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto ok = [&](int vec) {
+    bool r = al(Bpack, ldp, esz, vec) && al(dC, lddc, esz, vec);
+    if (local) r = r && al(B, ldb, esz, vec);
+    return r;
+  };
+#define SHIRO_SD(VEC, NCH, MASKED) return sddmm_launch<TB, VEC, NCH, MASKED>(P, prm, s);
+  if constexpr (std::is_same<TB, float>::value) {
+    if (N == 128 && ok(4)) SHIRO_SD(4, 1, false)
+    if (N == 256 && ok(4)) SHIRO_SD(4, 2, false)
+    if (N == 64 && ok(2)) SHIRO_SD(2, 1, false)
+  } else if constexpr (std::is_same<TB, double>::value) {
+    if (N == 64 && ok(2)) SHIRO_SD(2, 1, false)
+    if (N == 128 && ok(2)) SHIRO_SD(2, 2, false)
+  } else {
+    if (N == 256 && ok(8)) SHIRO_SD(8, 1, false)
+    if (N == 128 && ok(4)) SHIRO_SD(4, 1, false)
+    if (N == 64 && ok(2)) SHIRO_SD(2, 1, false)
+  }
+  if (N == 32) SHIRO_SD(1, 1, false)
+  if (N <= 32) SHIRO_SD(1, 1, true)
+  if (N <= 128) SHIRO_SD(1, 4, true)
+  if (N <= 512) SHIRO_SD(1, 16, true)
+#undef SHIRO_SD
+  SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "N=%d beyond the supported 512 columns", N);
+}
+
+shiro_status launch_sddmm(const shiro_plan_s* P, const void* dC, int64_t lddc, const void* Bpack,
+                          int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
+                          void* dA, cudaStream_t s) {
+  if (N < 0 || lddc < N || ldp < N) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "bad N or leading dimension");
+  if (P->nnz == 0) return SHIRO_OK;
+  if (!dA || !dC) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null dA or dC");
+  if (!Bpack && P->packed_rows > 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null Bpack");
+  if ((P->flags & SHIRO_PLAN_LOCAL_DIAG) && (!B || ldb < N))
+    SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "LOCAL_DIAG plan needs B with ldb >= N");
+  if (N == 0) {
+    const size_t vs = P->vdt == SHIRO_F64 ? 8 : 4;
+    SHIRO_CUDA(cudaMemsetAsync(dA, 0, vs * (size_t)P->nnz, s));
+    return SHIRO_OK;
+  }
+  if (P->vdt == SHIRO_F32 && dt == SHIRO_F32)
+    return sddmm_typed<float>(P, dC, lddc, Bpack, ldp, B, ldb, N, dA, s);
+  if (P->vdt == SHIRO_F32 && dt == SHIRO_BF16)
+    return sddmm_typed<__nv_bfloat16>(P, dC, lddc, Bpack, ldp, B, ldb, N, dA, s);
+  if (P->vdt == SHIRO_F64 && dt == SHIRO_F64)
+    return sddmm_typed<double>(P, dC, lddc, Bpack, ldp, B, ldb, N, dA, s);
+  SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "value/operand dtypes: F32 with F32 or BF16, or F64 with F64");
+}
+
+}  // namespace shiro
+
+using namespace shiro;
+
+extern "C" {
+
+shiro_status shiro_sddmm(shiro_plan_t plan, const void* dC, int64_t lddc, const void* Bpack,
+                         int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
+                         void* dA, void* stream) {
+  if (!plan) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  return launch_sddmm(plan, dC, lddc, Bpack, ldp, B, ldb, N, dt, dA, (cudaStream_t)stream);
+}
+
+shiro_status shiro_spmm_backward(shiro_plan_t plan, shiro_plan_t planT, const void* dC,
+                                 int64_t lddc, const void* Bpack, int64_t ldp, const void* B,
+                                 int64_t ldb, int32_t N, shiro_dtype dt, void* dCpack,
+                                 int64_t lddp, void* dB, int64_t lddb, void* dA, void* scratch,
+                                 size_t scratch_bytes, void* stream) {
+  if (!plan) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dB) {
+    if (!planT || !(planT->flags & SHIRO_PLAN_TRANSPOSE))
+      SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "dB needs the TRANSPOSE plan of the same matrix");
+    if (planT->M != plan->K || planT->K != plan->M || planT->nnz != plan->nnz)
+      SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "planT is not the transpose of plan");
+    SHIRO_TRY(launch_pack(planT, dC, lddc, N, dt, dCpack, lddp, s));
+    SHIRO_TRY(launch_spmm(planT, dCpack, lddp, dC, lddc, N, dt, dB, lddb, 0, scratch,
+                          scratch_bytes, s));
+  }
+  if (dA) SHIRO_TRY(launch_sddmm(plan, dC, lddc, Bpack, ldp, B, ldb, N, dt, dA, s));
+  return SHIRO_OK;
+}
+
+}  // extern "C"

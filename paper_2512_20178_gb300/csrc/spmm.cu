@@ -1,0 +1,468 @@
+// spmm.cu -- local SpMM over the packed B rows with aggregation over the tiles of a row block
+// (Sec. 2.2 stages 3-4, Sec. 5.1 stage 5), and the schedule autotuner.
+//
+// Design (HBM-bound gather, not a dense contraction, so no tensor cores):
+//   * one warp per work item; a dense row of B/C is spread over the 32 lanes in 4-16 byte
+//     vectors, so every B-row gather is one fully coalesced 128-512 byte warp load;
+//   * short rows are grouped into items and walked as one flat stream of nonzeros, so the
+//     U gathers of a batch are in flight together even when rows hold 1-3 nonzeros; the group's
+//     row pointers sit in lane registers (no dependent loads at row boundaries);
+//   * rows longer than long_row_nnz (power-law hubs) are cut into chunks whose FP32 partial sums
+//     go to scratch; the last chunk to arrive adds them in chunk order (deterministic, no float
+//     atomics, bounded FP32 summation length) and writes the C row;
+//   * all tiles of a row are summed in one pass in the row's stored order (ascending column
+//     blocks for column-sorted rows), so C is written once with streaming stores.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.cuh"
+#include "vec.cuh"
+
+namespace shiro {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename TV, typename TB>
+struct SpmmParams {
+  using TA = typename AccOf<TB>::T;
+  const int64_t* rowptr;
+  const int32_t* remap;
+  const TV* val;
+  const TB* Bpack;
+  int64_t ldp;
+  const TB* B;
+  int64_t ldb;
+  int32_t N;
+  TA* C;
+  int64_t ldc;
+  const Item* items;
+  int64_t n_items;
+  TA* scratch;
+  const int32_t* slot_lr;
+  const LongRow* lr;
+  int32_t* counters;
+  int32_t chunk;
+  int32_t accumulate;
+  int32_t persistent;
+  int* status;
+};
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
+__device__ __forceinline__ void gather_row(const SpmmParams<TV, TB>& p, int32_t idx,
+                                           typename AccOf<TB>::T (&b)[NCH][VEC], int lane) {
+  const TB* row = idx >= 0 ? p.Bpack + (int64_t)idx * p.ldp : p.B + (int64_t)(-1 - idx) * p.ldb;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int col = c * 32 * VEC + lane * VEC;
+    if (!MASKED || col < p.N) {
+      load_vec<TB, VEC, true>(row + col, b[c]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) b[c][v] = 0;
+    }
+  }
+}
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
+__device__ __forceinline__ void flush_row(const SpmmParams<TV, TB>& p, int32_t r,
+                                          typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
+  using TA = typename AccOf<TB>::T;
+  TA* c = p.C + (int64_t)r * p.ldc;
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int col = ch * 32 * VEC + lane * VEC;
+    if (!MASKED || col < p.N) {
+      if (p.accumulate) {
+        TA old[VEC];
+        load_acc_cg<TA, VEC>(c + col, old);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[ch][v] += old[v];
+      }
+      store_vec<TA, VEC, true>(c + col, acc[ch]);
+    }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[ch][v] = 0;
+  }
+}
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U>
+__device__ __forceinline__ void run_group(const SpmmParams<TV, TB>& p, const Item& item, int lane) {
+  using TA = typename AccOf<TB>::T;
+  const int32_t r0 = item.row, nr = item.tag;
+  const int64_t rp = lane < nr ? __ldg(p.rowptr + r0 + lane + 1) : 0;
+  const int64_t e_end = __shfl_sync(FULL, rp, nr - 1);
+  int32_t rl = 0;
+  int64_t next = __shfl_sync(FULL, rp, 0);
+  TA acc[NCH][VEC];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
+  for (int64_t e = item.e0; e < e_end; e += 32) {
+    const int n = (int)min((int64_t)32, e_end - e);
+    int32_t my_idx = 0;
+    TV my_val = 0;
+    if (lane < n) {
+      my_idx = __ldcs(p.remap + e + lane);
+      my_val = __ldcs(p.val + e + lane);
+    }
+    for (int j = 0; j < n; j += U) {
+      TA b[U][NCH][VEC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t idx = __shfl_sync(FULL, my_idx, (j + u) & 31);
+        if (j + u < n) gather_row<TV, TB, VEC, NCH, MASKED>(p, idx, b[u], lane);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const TV a = __shfl_sync(FULL, my_val, (j + u) & 31);
+        if (j + u < n) {
+          const int64_t ee = e + j + u;
+          while (ee >= next && rl < nr - 1) {
+            flush_row<TV, TB, VEC, NCH, MASKED>(p, r0 + rl, acc, lane);
+            ++rl;
+            next = __shfl_sync(FULL, rp, rl);
+          }
+#pragma unroll
+          for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[c][v] += (TA)a * b[u][c][v];
+        }
+      }
+    }
+  }
+  for (; rl < nr; ++rl) flush_row<TV, TB, VEC, NCH, MASKED>(p, r0 + rl, acc, lane);
+}
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U>
+__device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Item& item, int lane) {
+  using TA = typename AccOf<TB>::T;
+  const int32_t i = item.row;
+  const int32_t slot = -item.tag - 1;
+  const int64_t row_end = __ldg(p.rowptr + i + 1);
+  const int64_t e_end = min(item.e0 + (int64_t)p.chunk, row_end);
+  TA acc[NCH][VEC];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
+  for (int64_t e = item.e0; e < e_end; e += 32) {
+    const int n = (int)min((int64_t)32, e_end - e);
+    int32_t my_idx = 0;
+    TV my_val = 0;
+    if (lane < n) {
+      my_idx = __ldcs(p.remap + e + lane);
+      my_val = __ldcs(p.val + e + lane);
+    }
+    for (int j = 0; j < n; j += U) {
+      TA b[U][NCH][VEC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t idx = __shfl_sync(FULL, my_idx, (j + u) & 31);
+        if (j + u < n) gather_row<TV, TB, VEC, NCH, MASKED>(p, idx, b[u], lane);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const TV a = __shfl_sync(FULL, my_val, (j + u) & 31);
+        if (j + u < n) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[c][v] += (TA)a * b[u][c][v];
+        }
+      }
+    }
+  }
+  // Partial sum of this chunk, then arrival count; the last arrival adds the partials in order.
+  TA* part = p.scratch + (int64_t)slot * p.N;
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int col = c * 32 * VEC + lane * VEC;
+    if (!MASKED || col < p.N) store_acc_cg<TA, VEC>(part + col, acc[c]);
+  }
+  __threadfence();
+  const int32_t lr = __ldg(p.slot_lr + slot);
+  const LongRow L = p.lr[lr];
+  int old = 0;
+  if (lane == 0) old = atomicAdd(p.counters + lr, 1);
+  old = __shfl_sync(FULL, old, 0);
+  if (old == L.nchunks - 1) {
+    __threadfence();
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
+    for (int32_t s = 0; s < L.nchunks; ++s) {
+      const TA* q = p.scratch + (int64_t)(L.slot0 + s) * p.N;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const int col = c * 32 * VEC + lane * VEC;
+        if (!MASKED || col < p.N) {
+          TA t[VEC];
+          load_acc_cg<TA, VEC>(q + col, t);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) acc[c][v] += t[v];
+        }
+      }
+    }
+    flush_row<TV, TB, VEC, NCH, MASKED>(p, L.row, acc, lane);
+    if (lane == 0) p.counters[lr] = 0;
+  } else if (old >= L.nchunks) {
+    if (lane == 0) atomicOr(p.status, ST_COUNTER);
+  }
+}
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U>
+__global__ void __launch_bounds__(512) k_spmm(const SpmmParams<TV, TB> p) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  int64_t it = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int64_t step = p.persistent ? (int64_t)gridDim.x * wpb : p.n_items;
+  for (; it < p.n_items; it += step) {
+    const Item item = p.items[it];
+    if (item.tag > 0)
+      run_group<TV, TB, VEC, NCH, MASKED, U>(p, item, lane);
+    else
+      run_chunk<TV, TB, VEC, NCH, MASKED, U>(p, item, lane);
+  }
+}
+
+// ---- dispatch ----
+
+struct Variant {
+  int vec, nch, masked;
+};
+
+static bool aligned(const void* ptr, int64_t ld, size_t elem, int vec) {
+  const size_t a = std::min<size_t>(16, elem * (size_t)vec);
+  return ((uintptr_t)ptr % a) == 0 && ((size_t)ld * elem) % a == 0;
+}
+
+// Vector width and chunk count for N columns of storage dtype dt; all operands must honour the
+// alignment of the chosen vector width.
+static Variant pick_variant(shiro_dtype dt, int32_t N, bool ok16, bool ok8, bool ok4) {
+  if (dt == SHIRO_F32) {
+    if (ok16 && N % 128 == 0 && (N / 128 == 1 || N / 128 == 2 || N / 128 == 4)) return {4, N / 128, 0};
+    if (ok8 && N == 64) return {2, 1, 0};
+    if (N == 32) return {1, 1, 0};
+  } else if (dt == SHIRO_BF16) {
+    if (ok16 && N % 256 == 0 && (N / 256 == 1 || N / 256 == 2)) return {8, N / 256, 0};
+    if (ok8 && N == 128) return {4, 1, 0};
+    if (ok4 && N == 64) return {2, 1, 0};
+    if (N == 32) return {1, 1, 0};
+  } else {
+    if (ok16 && N % 64 == 0 && (N / 64 == 1 || N / 64 == 2 || N / 64 == 4)) return {2, N / 64, 0};
+    if (N == 32) return {1, 1, 0};
+  }
+  if (N <= 32) return {1, 1, 1};
+  if (N <= 128) return {1, 4, 1};
+  if (N <= 512) return {1, 16, 1};
+  return {0, 0, 0};
+}
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
+static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                               cudaStream_t s) {
+  constexpr int REG = VEC * NCH * (sizeof(typename AccOf<TB>::T) / 4);
+  constexpr int U = REG >= 16 ? 2 : (REG >= 8 ? 4 : 8);
+  auto kern = k_spmm<TV, TB, VEC, NCH, MASKED, U>;
+  const int wpc = P->opts.warps_per_cta;
+  const int threads = wpc * 32;
+  int64_t grid;
+  if (prm.persistent) {
+    int per_sm = 0;
+    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    grid = (int64_t)std::max(per_sm, 1) * P->sm_count;
+    grid = std::min<int64_t>(grid, (prm.n_items + wpc - 1) / wpc);
+  } else {
+    grid = (prm.n_items + wpc - 1) / wpc;
+  }
+  if (grid <= 0) return SHIRO_OK;
+  if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+  kern<<<(unsigned)grid, threads, 0, s>>>(prm);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
+template <typename TV, typename TB>
+static shiro_status dispatch(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm, Variant v,
+                             cudaStream_t s) {
+#define SHIRO_CASE(VEC, NCH, MASKED)                                        \
+  if (v.vec == VEC && v.nch == NCH && v.masked == MASKED)                   \
+    return launch_one<TV, TB, VEC, NCH, MASKED>(P, prm, s);
+  if constexpr (std::is_same<TB, float>::value) {
+    SHIRO_CASE(4, 1, 0) SHIRO_CASE(4, 2, 0) SHIRO_CASE(4, 4, 0) SHIRO_CASE(2, 1, 0)
+    SHIRO_CASE(1, 1, 0)
+  } else if constexpr (std::is_same<TB, double>::value) {
+    SHIRO_CASE(2, 1, 0) SHIRO_CASE(2, 2, 0) SHIRO_CASE(2, 4, 0) SHIRO_CASE(1, 1, 0)
+  } else {
+    SHIRO_CASE(8, 1, 0) SHIRO_CASE(8, 2, 0) SHIRO_CASE(4, 1, 0) SHIRO_CASE(2, 1, 0)
+    SHIRO_CASE(1, 1, 0)
+  }
+  SHIRO_CASE(1, 1, 1) SHIRO_CASE(1, 4, 1) SHIRO_CASE(1, 16, 1)
+#undef SHIRO_CASE
+  SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "no SpMM variant for N=%d", prm.N);
+}
+
+size_t spmm_scratch_bytes(const shiro_plan_s* P, int32_t N, shiro_dtype dt) {
+  if (!P->n_slots) return 0;
+  const size_t acc = dt == SHIRO_F64 ? 8 : 4;
+  return (size_t)P->n_slots * (size_t)N * acc + 256;
+}
+
+template <typename TV, typename TB>
+static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t ldp,
+                               const void* B, int64_t ldb, int32_t N, shiro_dtype dt, void* C,
+                               int64_t ldc, uint32_t flags, void* scratch, cudaStream_t s) {
+  using TA = typename AccOf<TB>::T;
+  SpmmParams<TV, TB> prm{};
+  prm.rowptr = P->rowptr;
+  prm.remap = P->d_remap;
+  prm.val = (const TV*)P->val;
+  prm.Bpack = (const TB*)Bpack;
+  prm.ldp = ldp;
+  prm.B = (const TB*)B;
+  prm.ldb = ldb;
+  prm.N = N;
+  prm.C = (TA*)C;
+  prm.ldc = ldc;
+  prm.items = P->d_items;
+  prm.n_items = P->n_items;
+  prm.scratch = (TA*)(scratch ? (void*)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) : nullptr);
+  prm.slot_lr = P->d_slot_lr;
+  prm.lr = P->d_lr;
+  prm.counters = P->d_counters;
+  prm.chunk = P->opts.chunk_nnz;
+  prm.accumulate = (flags & SHIRO_SPMM_ACCUMULATE) ? 1 : 0;
+  prm.persistent = P->opts.persistent;
+  prm.status = P->d_status;
+  const size_t esz = dtype_size(dt);
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto ok = [&](int vec) {
+    bool r = aligned(Bpack, ldp, esz, vec) && aligned(C, ldc, sizeof(TA), vec);
+    if (local) r = r && aligned(B, ldb, esz, vec);
+    return r;
+  };
+  const int v16 = (int)(16 / esz);
+  const Variant v = pick_variant(dt, N, ok(v16), ok(v16 / 2 ? v16 / 2 : 1), ok(v16 / 4 ? v16 / 4 : 1));
+  if (!v.vec) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "N=%d beyond the supported 512 columns", N);
+  return dispatch<TV, TB>(P, prm, v, s);
+}
+
+shiro_status launch_spmm(const shiro_plan_s* P, const void* Bpack, int64_t ldp, const void* B,
+                         int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
+                         uint32_t flags, void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  if (N < 0 || ldp < N || ldc < N) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "bad N or leading dimension");
+  if (!C && P->M > 0 && N > 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null C");
+  if (!Bpack && P->packed_rows > 0 && N > 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null Bpack");
+  if ((P->flags & SHIRO_PLAN_LOCAL_DIAG) && (!B || ldb < N))
+    SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "LOCAL_DIAG plan needs B with ldb >= N");
+  if (flags & ~SHIRO_SPMM_ACCUMULATE) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "unknown SpMM flags");
+  const size_t need = spmm_scratch_bytes(P, N, dt);
+  if (need && (!scratch || scratch_bytes < need))
+    SHIRO_FAIL(SHIRO_ERR_INSUFFICIENT_WORKSPACE, "SpMM scratch of %zu bytes, need %zu",
+               scratch_bytes, need);
+  if (N == 0 || P->M == 0) return SHIRO_OK;
+  if (P->vdt == SHIRO_F32 && dt == SHIRO_F32)
+    return spmm_typed<float, float>(P, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, s);
+  if (P->vdt == SHIRO_F32 && dt == SHIRO_BF16)
+    return spmm_typed<float, __nv_bfloat16>(P, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch,
+                                            s);
+  if (P->vdt == SHIRO_F64 && dt == SHIRO_F64)
+    return spmm_typed<double, double>(P, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, s);
+  SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "value/operand dtypes: F32 with F32 or BF16, or F64 with F64");
+}
+
+}  // namespace shiro
+
+using namespace shiro;
+
+extern "C" {
+
+shiro_status shiro_spmm_scratch(shiro_plan_t plan, int32_t N, shiro_dtype dt, size_t* bytes) {
+  if (!plan || !bytes || N < 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "bad arguments");
+  *bytes = spmm_scratch_bytes(plan, N, dt);
+  return SHIRO_OK;
+}
+
+shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
+                        int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
+                        uint32_t flags, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!plan) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  return launch_spmm(plan, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, scratch_bytes,
+                     (cudaStream_t)stream);
+}
+
+shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, const void* B,
+                            int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
+                            void* scratch, size_t scratch_bytes, int32_t reps, void* stream,
+                            shiro_opts* best) {
+  if (!P) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (reps < 1) reps = 3;
+  const shiro_opts start = P->opts;
+  // Candidate schedules from N and the degree profile: average nonzeros per row sets the group
+  // size, the largest rows decide whether splitting matters at all.
+  const double avg = P->M ? (double)P->nnz / (double)P->M : 0.0;
+  std::vector<shiro_opts> cands;
+  const int32_t groups[] = {32, 64, 128, 256};
+  const int32_t chunks[] = {256, 512, 1024};
+  const int32_t warps[] = {4, 8};
+  for (int32_t gn : groups) {
+    if (gn < avg / 2) continue;
+    for (int32_t ch : chunks) {
+      if (P->max_row_nnz <= ch && ch != 512) continue;
+      for (int32_t w : warps) {
+        for (int32_t pers = 0; pers < 2; ++pers) {
+          shiro_opts o = start;
+          o.group_nnz = gn;
+          o.group_rows = 32;
+          o.chunk_nnz = ch;
+          o.long_row_nnz = 2 * ch;
+          o.warps_per_cta = w;
+          o.persistent = pers;
+          cands.push_back(o);
+        }
+      }
+    }
+  }
+  cands.push_back(start);
+  cudaEvent_t e0, e1;
+  SHIRO_CUDA(cudaEventCreate(&e0));
+  SHIRO_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  shiro_opts best_o = start;
+  shiro_status st = SHIRO_OK;
+  for (const shiro_opts& o : cands) {
+    st = build_schedule(P, o, s);
+    if (st != SHIRO_OK) break;
+    if (spmm_scratch_bytes(P, N, dt) > scratch_bytes) continue;
+    st = launch_spmm(P, Bpack, ldp, B, ldb, N, dt, C, ldc, 0, scratch, scratch_bytes, s);
+    if (st != SHIRO_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) {
+      st = launch_spmm(P, Bpack, ldp, B, ldb, N, dt, C, ldc, 0, scratch, scratch_bytes, s);
+      if (st != SHIRO_OK) break;
+    }
+    if (st != SHIRO_OK) break;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = SHIRO_ERR_CUDA; set_error("autotune sync failed"); break; }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_o = o;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SHIRO_OK) {
+    build_schedule(P, start, s);
+    return st;
+  }
+  SHIRO_TRY(build_schedule(P, best_o, s));
+  if (best) *best = best_o;
+  return SHIRO_OK;
+}
+
+}  // extern "C"

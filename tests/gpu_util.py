@@ -1,0 +1,99 @@
+"""Helpers of the GPU parity tests: inputs to the device, oracle comparisons, tolerances.
+
+Tolerance (the benchmark spec): FP32 SpMM within max scaled error 1e-5 of the FP64 oracle, the error of
+element (i, k) being |C_ik - C64_ik| / sum_j |a_ij| |b_jk| (and exact zeros where the scale is 0).
+The same bound is applied to dB (scale sum |a_ij| |dC_ik|) and dA (scale sum_k |dC_ik| |B_jk|).
+BF16-stored operands are compared with the oracle run on the BF16-rounded values, which FP64
+represents exactly, so the same 1e-5 bound applies to the FP32 accumulation.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2512_20178_gb300 import synth
+
+TOL = 1e-5
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2512_20178_gb300 import shiro
+    return shiro
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def to_dev(A: synth.CSR, vdt=torch.float32):
+    d = dev()
+    return (torch.from_numpy(np.ascontiguousarray(A.rowptr)).to(d),
+            torch.from_numpy(np.ascontiguousarray(A.col)).to(d),
+            torch.from_numpy(np.ascontiguousarray(A.val)).to(d).to(vdt))
+
+
+def plan_of(A, Pr=1, Pc=1, flags=0, opts=None, vdt=torch.float32, row_bounds=None,
+            col_bounds=None):
+    shiro = lib()
+    rp, col, val = to_dev(A, vdt)
+    return shiro.Plan.create(rp, col, val, A.M, A.K, Pr, Pc, row_bounds=row_bounds,
+                             col_bounds=col_bounds, flags=flags, opts=opts)
+
+
+def assert_plan_matches(P, A, Pr, Pc, flags=0, rb=None, cb=None):
+    """Integer outputs of the plan equal the oracle's bit for bit."""
+    shiro = lib()
+    diag_only = bool(flags & shiro.SHIRO_PLAN_DIAG_ONLY)
+    local = bool(flags & shiro.SHIRO_PLAN_LOCAL_DIAG)
+    O = oracle.plan(A, Pr, Pc, rb=rb, cb=cb, diag_only=diag_only)
+    st = P.tile_stats()
+    assert np.array_equal(st["tile_nnz"].numpy(), O.tile_nnz), "tile nnz"
+    assert np.array_equal(st["tile_nrows"].numpy(), O.tile_nrows), "|Rows|"
+    assert np.array_equal(st["tile_ncols"].numpy(), O.tile_ncols), "|Cols|"
+    assert np.array_equal(st["tile_cols_ptr"].numpy(), O.tile_cols_ptr), "tile_cols_ptr"
+    pack_ptr, pack_src = O.pack_layout(local)
+    assert np.array_equal(st["pack_ptr"].numpy(), pack_ptr), "pack_ptr"
+    ex = P.export()
+    torch.cuda.synchronize()
+    assert np.array_equal(ex["cols_sorted"].cpu().numpy(), O.cols_sorted), "Cols (sorted)"
+    assert np.array_equal(ex["pack_src"].cpu().numpy(), pack_src), "pack list"
+    assert np.array_equal(ex["colidx_local"].cpu().numpy(), O.colidx_local), "colidx_local"
+    # remap: packed row, or -1 - col for local diagonal tiles.
+    rows = A.row_ids()
+    p = np.searchsorted(O.rb, rows, side="right") - 1
+    q = np.searchsorted(O.cb, A.col, side="right") - 1
+    t = p if diag_only else p * Pc + q
+    expect = pack_ptr[t] + O.colidx_local
+    if local:
+        expect = np.where(p == q, -1 - A.col.astype(np.int64), expect)
+    assert np.array_equal(ex["remap"].cpu().numpy(), expect.astype(np.int32)), "remap"
+    vb, vc, vr = P.volumes(32, torch.float32)
+    ob, oc = O.volumes(32, 4)
+    assert np.array_equal(vb.numpy(), ob) and np.array_equal(vc.numpy(), oc), "volumes"
+    assert np.array_equal(vr.numpy(), O.tile_nrows * 32 * 4)
+    return O
+
+
+def scaled_err(C, C64, S):
+    return oracle.scaled_error(C, C64, S)
+
+
+def check_spmm(A, B_host, C_dev, rows=None, tol=TOL):
+    """Scaled error of the GPU C against the FP64 oracle (optionally on sampled rows)."""
+    C = C_dev.detach().cpu().numpy()
+    if rows is not None:
+        C = C[rows]
+    C64 = oracle.spmm(A, B_host, rows=rows)
+    S = oracle.abs_scale(A, B_host, rows=rows)
+    err = scaled_err(C, C64, S)
+    assert err <= tol, f"scaled error {err:.3e} > {tol}"
+    return err

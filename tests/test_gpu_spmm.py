@@ -1,0 +1,152 @@
+"""Pack and SpMM parity on the GPU against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2512_20178_gb300 import synth
+import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+def setup_module(_):
+    gu.need_gpu()
+
+
+def run(A, B, Pr=1, Pc=1, flags=0, opts=None):
+    P = gu.plan_of(A, Pr, Pc, flags, opts=opts)
+    Bd = torch.from_numpy(B).to(gu.dev())
+    Bp = P.pack(Bd)
+    C = P.spmm(Bp, B=Bd)
+    torch.cuda.synchronize()
+    return P, Bd, Bp, C
+
+
+SMALL_SPLIT = dict(long_row_nnz=64, chunk_nnz=32, group_nnz=40, group_rows=7)
+
+
+@pytest.mark.parametrize("N", [1, 7, 32, 33, 64, 100, 128, 256, 512])
+def test_spmm_n_sweep(N):
+    A = synth.rmat(12, 8, 21)
+    B = synth.dense_normal(A.K, N, 22)
+    shiro = gu.lib()
+    P, Bd, Bp, C = run(A, B, 4, 4, opts=shiro.make_opts(**SMALL_SPLIT))
+    assert P.info.n_long_rows > 0
+    src = P.export()["pack_src"].cpu().numpy()
+    assert np.array_equal(Bp.cpu().numpy(), B[src]), "pack is not bit-exact"
+    gu.check_spmm(A, B, C)
+
+
+@pytest.mark.parametrize("name", ["er4096_2d", "er4096_1d_local", "ragged", "more_blocks",
+                                  "empty_rows", "rmat14_default"])
+def test_spmm_cases(name):
+    shiro = gu.lib()
+    flags = 0
+    if name.startswith("er4096"):
+        A, Pr, Pc, N = synth.er(4096, 8, 1), 4, 4, 32
+        if name.endswith("local"):
+            flags = shiro.SHIRO_PLAN_LOCAL_DIAG
+    elif name == "ragged":
+        A, Pr, Pc, N = synth.random_small(1000, 777, 0.01, 11), 3, 5, 64
+    elif name == "more_blocks":
+        A, Pr, Pc, N = synth.random_small(5, 9, 0.5, 13), 8, 8, 128
+    elif name == "empty_rows":
+        A, Pr, Pc, N = synth.random_small(300, 300, 0.02, 14, empty_rows=150), 2, 2, 128
+    else:
+        A, Pr, Pc, N = synth.rmat(14, 16, 3), 4, 4, 128
+    B = synth.dense_normal(A.K, N, 5)
+    P, Bd, Bp, C = run(A, B, Pr, Pc, flags)
+    gu.check_spmm(A, B, C)
+    # Packed path == direct path in FP64 (the oracle's own consistency at these inputs).
+    O = oracle.plan(A, Pr, Pc)
+    _, src = O.pack_layout(bool(flags))
+    C1 = oracle.spmm_packed(A, O, B[src], B, bool(flags))
+    assert np.array_equal(C1, oracle.spmm(A, B))
+
+
+def test_empty_matrix_gives_zero_rows():
+    A = synth.CSR(64, 32, np.zeros(65, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    B = synth.dense_normal(32, 128, 1)
+    _, _, _, C = run(A, B, 2, 2)
+    assert torch.count_nonzero(C).item() == 0
+
+
+def test_hub_row_2e17_fp32_summation():
+    """One row with 2^17 nonzeros: split into chunks, partial sums added in order."""
+    A = synth.hub_matrix(64, 1 << 17, 5, 1 << 17, 2, 14)
+    B = synth.dense_normal(A.K, 128, 15)
+    P, Bd, Bp, C = run(A, B, 2, 4)
+    assert P.info.n_long_rows >= 1
+    err = gu.check_spmm(A, B, C)
+    print("hub-row scaled error", err)
+
+
+def test_accumulate_doubles_exactly():
+    shiro = gu.lib()
+    A = synth.rmat(12, 8, 31)
+    B = synth.dense_normal(A.K, 128, 32)
+    P, Bd, Bp, C = run(A, B, 2, 2, opts=shiro.make_opts(**SMALL_SPLIT))
+    C2 = C.clone()
+    P.spmm(Bp, B=Bd, out=C2, accumulate=True)
+    torch.cuda.synchronize()
+    assert torch.equal(C2, 2 * C)
+
+
+def test_deterministic_and_persistent_identical():
+    shiro = gu.lib()
+    A = synth.rmat(14, 16, 41)
+    B = synth.dense_normal(A.K, 128, 42)
+    P, Bd, Bp, C = run(A, B, 4, 4, opts=shiro.make_opts(long_row_nnz=256, chunk_nnz=128))
+    C_again = P.spmm(Bp, B=Bd)
+    P.reschedule(persistent=1)
+    C_pers = P.spmm(Bp, B=Bd)
+    torch.cuda.synchronize()
+    assert torch.equal(C, C_again), "SpMM not deterministic"
+    assert torch.equal(C, C_pers), "persistent schedule changed the result"
+
+
+def test_scratch_too_small_rejected():
+    shiro = gu.lib()
+    A = synth.rmat(12, 8, 21)
+    P = gu.plan_of(A, 2, 2, opts=shiro.make_opts(**SMALL_SPLIT))
+    Bd = torch.from_numpy(synth.dense_normal(A.K, 64, 1)).to(gu.dev())
+    Bp = P.pack(Bd)
+    small = torch.empty(16, dtype=torch.uint8, device=gu.dev())
+    with pytest.raises(shiro.ShiroError) as ei:
+        P.spmm(Bp, scratch=small)
+    assert ei.value.status == 3
+
+
+def test_autotune_keeps_result():
+    A = synth.rmat(14, 16, 51)
+    B = synth.dense_normal(A.K, 128, 52)
+    P, Bd, Bp, C = run(A, B, 4, 4)
+    best = P.autotune(Bp, B=Bd, reps=1)
+    C2 = P.spmm(Bp, B=Bd)
+    torch.cuda.synchronize()
+    assert best["chunk_nnz"] >= 32
+    gu.check_spmm(A, B, C2)
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    A = synth.rmat(20, 16, 2)
+    B = synth.dense_normal(A.K, 128, 2)
+    return A, B
+
+
+def test_full_size_rmat20_sampled_rows(rmat20):
+    """The benchmark workload (R-MAT 2^20, N=128, 4x4 tiles, default schedule): sampled rows."""
+    A, B = rmat20
+    P, Bd, Bp, C = run(A, B, 4, 4)
+    deg = np.diff(A.rowptr)
+    rng_rows = (synth.uniform_f64(9, synth.STREAM_PERM, 0, 2000) * A.M).astype(np.int64)
+    hubs = np.argsort(deg)[-64:]
+    empties = np.nonzero(deg == 0)[0][:64]
+    rows = np.unique(np.concatenate([rng_rows, hubs, empties, [0, A.M - 1]]))
+    gu.check_spmm(A, B, C, rows=rows)
+    # Packed rows are bit-exact copies (sampled).
+    src = P.export()["pack_src"].cpu().numpy()
+    pick = np.unique((synth.uniform_f64(10, synth.STREAM_PERM, 0, 4000) * len(src)).astype(np.int64))
+    assert np.array_equal(Bp[torch.from_numpy(pick).to(gu.dev())].cpu().numpy(), B[src[pick]])

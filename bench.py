@@ -200,7 +200,12 @@ def run_reference(args):
     import oracle
     A, B = workload(args)
     oracle.build()
-    stride = 16
+    # Size the per-step row sample so that warmup + steps take about two minutes in total.
+    probe = cpu_baseline(A, B, args, 256)
+    per_step = 120.0 / max(1, args.warmup + args.steps)
+    stride = 256
+    while stride > 8 and probe["seconds"] * 256 / (stride // 2) <= per_step:
+        stride //= 2
     res = None
     ts = []
     for k in range(args.warmup + args.steps):

@@ -92,8 +92,12 @@ typedef struct {
   int32_t chunk_nnz;
   int32_t group_nnz;
   int32_t group_rows;
-  int32_t warps_per_cta; /* 1..16 */
+  int32_t warps_per_cta; /* 1..8 */
   int32_t persistent;    /* 1: grid = SMs x resident CTAs and warps stride over the items */
+  int32_t pipeline;      /* 1: B-row gathers staged through shared memory by asynchronous copies
+                            (two stages per warp); 0: gathers into registers */
+  int32_t stage_rows;    /* rows per stage with pipeline 1: 8, 16 or 32 (0 = the largest that keeps
+                            a stage within 16 KB) */
 } shiro_opts;
 
 /* Bytes of workspace shiro_plan_create needs for A and this partition (an upper bound that does

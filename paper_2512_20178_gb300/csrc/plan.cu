@@ -38,12 +38,15 @@ shiro_status resolve_opts(const shiro_opts* in, shiro_opts* o) {
     if (in->group_rows) o->group_rows = in->group_rows;
     if (in->warps_per_cta) o->warps_per_cta = in->warps_per_cta;
     o->persistent = in->persistent;
+    o->pipeline = in->pipeline;
+    o->stage_rows = in->stage_rows;
   }
   if (o->chunk_nnz < 32 || o->long_row_nnz < o->chunk_nnz || o->group_nnz < 1 ||
-      o->group_rows < 1 || o->group_rows > 32 || o->warps_per_cta < 1 || o->warps_per_cta > 16)
+      o->group_rows < 1 || o->group_rows > 32 || o->warps_per_cta < 1 || o->warps_per_cta > 8 ||
+      (o->stage_rows != 0 && o->stage_rows != 8 && o->stage_rows != 16 && o->stage_rows != 32))
     SHIRO_FAIL(SHIRO_ERR_INVALID_ARG,
                "bad schedule options: need 32 <= chunk_nnz <= long_row_nnz, group_nnz >= 1, "
-               "1 <= group_rows <= 32, 1 <= warps_per_cta <= 16");
+               "1 <= group_rows <= 32, 1 <= warps_per_cta <= 8, stage_rows in {0, 8, 16, 32}");
   return SHIRO_OK;
 }
 
@@ -593,6 +596,8 @@ void shiro_default_opts(shiro_opts* o) {
   o->group_rows = 32;
   o->warps_per_cta = 8;
   o->persistent = 0;
+  o->pipeline = 1;
+  o->stage_rows = 0;
 }
 
 const char* shiro_last_error(void) { return g_err.c_str(); }

@@ -20,7 +20,7 @@
 
 namespace shiro {
 
-constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned FULL_MASK = 0xffffffffu;
 
 template <typename TV, typename TB>
 struct SpmmParams {
@@ -41,21 +41,26 @@ struct SpmmParams {
   const int32_t* slot_lr;
   const LongRow* lr;
   int32_t* counters;
+  int64_t n_chunk_items;
+  int64_t chunk_blocks;
   int32_t chunk;
   int32_t accumulate;
   int32_t persistent;
   int* status;
 };
 
+// (index, value) of one nonzero as staged in shared memory; two FP32 entries fill 16 bytes.
+template <typename TV> struct Pair { int32_t idx; float val; };
+template <> struct Pair<double> { int32_t idx; int32_t pad; double val; };
+
 template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
-__device__ __forceinline__ void gather_row(const SpmmParams<TV, TB>& p, int32_t idx,
+__device__ __forceinline__ void gather_row(const SpmmParams<TV, TB>& p, const TB* row,
                                            typename AccOf<TB>::T (&b)[NCH][VEC], int lane) {
-  const TB* row = idx >= 0 ? p.Bpack + (int64_t)idx * p.ldp : p.B + (int64_t)(-1 - idx) * p.ldb;
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
     const int col = c * 32 * VEC + lane * VEC;
     if (!MASKED || col < p.N) {
-      load_vec<TB, VEC, true>(row + col, b[c]);
+      load_vec<TB, VEC, true>(row + c * 32 * VEC, b[c]);
     } else {
 #pragma unroll
       for (int v = 0; v < VEC; ++v) b[c][v] = 0;
@@ -85,95 +90,129 @@ __device__ __forceinline__ void flush_row(const SpmmParams<TV, TB>& p, int32_t r
   }
 }
 
-template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U>
-__device__ __forceinline__ void run_group(const SpmmParams<TV, TB>& p, const Item& item, int lane) {
+// Lane-local view of the dense operands: row r of the packed buffer starts at bp + r * ldp
+// (32-bit index times 32-bit stride, one wide multiply-add per gather).
+template <typename TB>
+struct Bases {
+  const TB* bp;
+  const TB* b;
+  uint32_t ldp, ldb;
+};
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool LOCAL, bool FULL>
+__device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
+                                           const Pair<TV>* sp, int n, int off, int32_t r0, int nr,
+                                           int rel, unsigned endmask,
+                                           typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
+  using TA = typename AccOf<TB>::T;
+#pragma unroll 1
+  for (int j = 0; j < (FULL ? 32 : n); j += U) {
+    TA b[U][NCH][VEC];
+    TV a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (FULL || j + u < n) {
+        const Pair<TV> pr = sp[j + u];
+        a[u] = (TV)pr.val;
+        const TB* row;
+        if (LOCAL && pr.idx < 0)
+          row = bs.b + (uint64_t)(uint32_t)(-1 - pr.idx) * bs.ldb;
+        else
+          row = bs.bp + (uint64_t)(uint32_t)pr.idx * bs.ldp;
+        gather_row<TV, TB, VEC, NCH, MASKED>(p, row, b[u], lane);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (FULL || j + u < n) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) acc[c][v] = fma((TA)a[u], b[u][c][v], acc[c][v]);
+        if ((endmask >> (j + u)) & 1u) {
+          // The nonzero at off + j + u ends a non-empty row: the first lane whose row end is here.
+          const unsigned who = __ballot_sync(FULL_MASK, lane < nr && rel == off + j + u + 1);
+          flush_row<TV, TB, VEC, NCH, MASKED>(p, r0 + __ffs(who) - 1, acc, lane);
+        }
+      }
+    }
+  }
+}
+
+// Accumulates nonzeros [base, base + total) of rows r0 .. r0 + nr - 1.  Lane l < nr holds the
+// end of row r0 + l relative to base in `rel` and whether that row is non-empty; the end of every
+// non-empty row is flushed to C as the stream passes it (chunks of long rows pass nr = 0 and
+// flush nothing).  The (index, value) pairs of each batch of 32 go through shared memory and the
+// next batch's pairs are loaded while the current batch's gathers are in flight.
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool LOCAL>
+__device__ __forceinline__ void spmm_span(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
+                                          Pair<TV>* sp, int64_t base, int total, int32_t r0,
+                                          int nr, int rel, bool nonempty,
+                                          typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
+  int32_t nidx = 0;
+  TV nval = 0;
+  if (lane < total) {
+    nidx = __ldcs(p.remap + base + lane);
+    nval = __ldcs(p.val + base + lane);
+  }
+  for (int off = 0; off < total; off += 32) {
+    const int n = min(32, total - off);
+    __syncwarp();
+    Pair<TV> pr;
+    pr.idx = nidx;
+    pr.val = nval;
+    sp[lane] = pr;
+    __syncwarp();
+    if (off + 32 + lane < total) {
+      nidx = __ldcs(p.remap + base + off + 32 + lane);
+      nval = __ldcs(p.val + base + off + 32 + lane);
+    }
+    const int q = rel - 1 - off;
+    const unsigned bit = (lane < nr && nonempty && q >= 0 && q < 32) ? (1u << q) : 0u;
+    const unsigned endmask = __reduce_or_sync(FULL_MASK, bit);
+    if (n == 32)
+      spmm_batch<TV, TB, VEC, NCH, MASKED, U, LOCAL, true>(p, bs, sp, n, off, r0, nr, rel, endmask,
+                                                           acc, lane);
+    else
+      spmm_batch<TV, TB, VEC, NCH, MASKED, U, LOCAL, false>(p, bs, sp, n, off, r0, nr, rel,
+                                                            endmask, acc, lane);
+  }
+}
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool LOCAL>
+__device__ __forceinline__ void run_group(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
+                                          Pair<TV>* sp, const Item& item, int lane) {
   using TA = typename AccOf<TB>::T;
   const int32_t r0 = item.row, nr = item.tag;
   const int64_t rp = lane < nr ? __ldg(p.rowptr + r0 + lane + 1) : 0;
-  const int64_t e_end = __shfl_sync(FULL, rp, nr - 1);
-  int32_t rl = 0;
-  int64_t next = __shfl_sync(FULL, rp, 0);
+  const int rel = (int)(rp - item.e0);
+  const int prev = __shfl_up_sync(FULL_MASK, rel, 1);
+  const bool nonempty = lane < nr && rel > (lane ? prev : 0);
+  const int total = __shfl_sync(FULL_MASK, rel, nr - 1);
   TA acc[NCH][VEC];
 #pragma unroll
   for (int c = 0; c < NCH; ++c)
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
-  for (int64_t e = item.e0; e < e_end; e += 32) {
-    const int n = (int)min((int64_t)32, e_end - e);
-    int32_t my_idx = 0;
-    TV my_val = 0;
-    if (lane < n) {
-      my_idx = __ldcs(p.remap + e + lane);
-      my_val = __ldcs(p.val + e + lane);
-    }
-    for (int j = 0; j < n; j += U) {
-      TA b[U][NCH][VEC];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int32_t idx = __shfl_sync(FULL, my_idx, (j + u) & 31);
-        if (j + u < n) gather_row<TV, TB, VEC, NCH, MASKED>(p, idx, b[u], lane);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const TV a = __shfl_sync(FULL, my_val, (j + u) & 31);
-        if (j + u < n) {
-          const int64_t ee = e + j + u;
-          while (ee >= next && rl < nr - 1) {
-            flush_row<TV, TB, VEC, NCH, MASKED>(p, r0 + rl, acc, lane);
-            ++rl;
-            next = __shfl_sync(FULL, rp, rl);
-          }
-#pragma unroll
-          for (int c = 0; c < NCH; ++c)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] += (TA)a * b[u][c][v];
-        }
-      }
+  // Empty rows get zeros up front (C += 0 leaves them unchanged when accumulating).
+  if (!p.accumulate) {
+    unsigned empty = __ballot_sync(FULL_MASK, lane < nr && !nonempty);
+    while (empty) {
+      const int l = __ffs(empty) - 1;
+      empty &= empty - 1;
+      flush_row<TV, TB, VEC, NCH, MASKED>(p, r0 + l, acc, lane);
     }
   }
-  for (; rl < nr; ++rl) flush_row<TV, TB, VEC, NCH, MASKED>(p, r0 + rl, acc, lane);
+  spmm_span<TV, TB, VEC, NCH, MASKED, U, LOCAL>(p, bs, sp, item.e0, total, r0, nr, rel, nonempty,
+                                                acc, lane);
 }
 
-template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U>
-__device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Item& item, int lane) {
+// Partial sum of one chunk of a long row, then its arrival count; the last chunk to arrive adds
+// the row's partials in chunk order and writes the C row.
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
+__device__ __forceinline__ void finish_chunk(const SpmmParams<TV, TB>& p, int32_t slot,
+                                             typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
   using TA = typename AccOf<TB>::T;
-  const int32_t i = item.row;
-  const int32_t slot = -item.tag - 1;
-  const int64_t row_end = __ldg(p.rowptr + i + 1);
-  const int64_t e_end = min(item.e0 + (int64_t)p.chunk, row_end);
-  TA acc[NCH][VEC];
-#pragma unroll
-  for (int c = 0; c < NCH; ++c)
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
-  for (int64_t e = item.e0; e < e_end; e += 32) {
-    const int n = (int)min((int64_t)32, e_end - e);
-    int32_t my_idx = 0;
-    TV my_val = 0;
-    if (lane < n) {
-      my_idx = __ldcs(p.remap + e + lane);
-      my_val = __ldcs(p.val + e + lane);
-    }
-    for (int j = 0; j < n; j += U) {
-      TA b[U][NCH][VEC];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int32_t idx = __shfl_sync(FULL, my_idx, (j + u) & 31);
-        if (j + u < n) gather_row<TV, TB, VEC, NCH, MASKED>(p, idx, b[u], lane);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const TV a = __shfl_sync(FULL, my_val, (j + u) & 31);
-        if (j + u < n) {
-#pragma unroll
-          for (int c = 0; c < NCH; ++c)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[c][v] += (TA)a * b[u][c][v];
-        }
-      }
-    }
-  }
-  // Partial sum of this chunk, then arrival count; the last arrival adds the partials in order.
   TA* part = p.scratch + (int64_t)slot * p.N;
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
@@ -185,7 +224,7 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Ite
   const LongRow L = p.lr[lr];
   int old = 0;
   if (lane == 0) old = atomicAdd(p.counters + lr, 1);
-  old = __shfl_sync(FULL, old, 0);
+  old = __shfl_sync(FULL_MASK, old, 0);
   if (old == L.nchunks - 1) {
     __threadfence();
 #pragma unroll
@@ -212,18 +251,67 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Ite
   }
 }
 
-template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U>
-__global__ void __launch_bounds__(512) k_spmm(const SpmmParams<TV, TB> p) {
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool LOCAL>
+__device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
+                                          Pair<TV>* sp, const Item& item, int lane) {
+  using TA = typename AccOf<TB>::T;
+  const int32_t i = item.row;
+  const int32_t slot = -item.tag - 1;
+  const int64_t row_end = __ldg(p.rowptr + i + 1);
+  const int total = (int)min((int64_t)p.chunk, row_end - item.e0);
+  TA acc[NCH][VEC];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
+  spmm_span<TV, TB, VEC, NCH, MASKED, U, LOCAL>(p, bs, sp, item.e0, total, i, 0, 0, false, acc,
+                                                lane);
+  finish_chunk<TV, TB, VEC, NCH, MASKED>(p, slot, acc, lane);
+}
+
+}  // namespace shiro
+
+#include "spmm_async.cuh"
+
+namespace shiro {
+
+template <int VEC, int NCH, typename TB>
+struct Occupancy {
+  // Registers per lane held by one gathered row fragment.
+  static constexpr int REG = VEC * NCH * (int)(sizeof(typename AccOf<TB>::T) / 4);
+  static constexpr int U = REG >= 16 ? 2 : 4;
+  static constexpr int MIN_BLOCKS = REG <= 4 ? 3 : 2;
+};
+
+// Blocks [0, chunk_blocks) run the chunks of long rows, the others the row groups (the two
+// paths share no loop, so each gets its own register allocation).  Items hold the chunks first.
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool LOCAL>
+__global__ void __launch_bounds__(256, (Occupancy<VEC, NCH, TB>::MIN_BLOCKS))
+    k_spmm(const SpmmParams<TV, TB> p) {
+  __shared__ Pair<TV> s_pairs[8][32];
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  int64_t it = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
-  const int64_t step = p.persistent ? (int64_t)gridDim.x * wpb : p.n_items;
-  for (; it < p.n_items; it += step) {
-    const Item item = p.items[it];
-    if (item.tag > 0)
-      run_group<TV, TB, VEC, NCH, MASKED, U>(p, item, lane);
-    else
-      run_chunk<TV, TB, VEC, NCH, MASKED, U>(p, item, lane);
+  Bases<TB> bs;
+  bs.bp = p.Bpack + lane * VEC;
+  bs.b = p.B + lane * VEC;
+  bs.ldp = (uint32_t)p.ldp;
+  bs.ldb = (uint32_t)p.ldb;
+  Pair<TV>* sp = s_pairs[warp];
+  if ((int64_t)blockIdx.x < p.chunk_blocks) {
+    const int64_t step = (int64_t)p.chunk_blocks * wpb;
+    for (int64_t it = (int64_t)blockIdx.x * wpb + warp; it < p.n_chunk_items; it += step) {
+      const Item item = p.items[it];
+      run_chunk<TV, TB, VEC, NCH, MASKED, U, LOCAL>(p, bs, sp, item, lane);
+    }
+  } else {
+    const int64_t nb = (int64_t)gridDim.x - p.chunk_blocks;
+    const int64_t step = p.persistent ? nb * wpb : p.n_items;
+    for (int64_t it = p.n_chunk_items + ((int64_t)blockIdx.x - p.chunk_blocks) * wpb + warp;
+         it < p.n_items; it += step) {
+      const Item item = p.items[it];
+      run_group<TV, TB, VEC, NCH, MASKED, U, LOCAL>(p, bs, sp, item, lane);
+    }
   }
 }
 
@@ -260,26 +348,72 @@ static Variant pick_variant(shiro_dtype dt, int32_t N, bool ok16, bool ok8, bool
   return {0, 0, 0};
 }
 
+template <typename TV, typename TB, int VEC, int NCH, int BATCH>
+static shiro_status launch_async_batch(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                       cudaStream_t s) {
+  using L = AsyncLayout<TV, TB, VEC, NCH, BATCH>;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm_async<TV, TB, VEC, NCH, BATCH, true>
+                    : k_spmm_async<TV, TB, VEC, NCH, BATCH, false>;
+  const int max_smem = 227 * 1024;
+  const int wpc = std::max(1, std::min(P->opts.warps_per_cta, max_smem / L::WARP));
+  const int smem = wpc * L::WARP;
+  SHIRO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.chunk_blocks = (q.n_chunk_items + wpc - 1) / wpc;
+  const int64_t n_groups = prm.n_items - q.n_chunk_items;
+  int64_t gblocks = (n_groups + wpc - 1) / wpc;
+  if (prm.persistent) {
+    int per_sm = 0;
+    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, smem));
+    gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
+  }
+  const int64_t grid = q.chunk_blocks + gblocks;
+  if (grid <= 0) return SHIRO_OK;
+  if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+  kern<<<(unsigned)grid, wpc * 32, smem, s>>>(q);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
+template <typename TV, typename TB, int VEC, int NCH>
+static shiro_status launch_async(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                 cudaStream_t s) {
+  constexpr int ROW = 32 * VEC * NCH * (int)sizeof(TB);
+  int batch = P->opts.stage_rows ? P->opts.stage_rows : 32;
+  while (batch > 8 && batch * ROW > 16384) batch /= 2;
+  if (batch >= 32 && 32 * ROW <= 16384) return launch_async_batch<TV, TB, VEC, NCH, 32>(P, prm, s);
+  if (batch >= 16 && 16 * ROW <= 16384) return launch_async_batch<TV, TB, VEC, NCH, 16>(P, prm, s);
+  return launch_async_batch<TV, TB, VEC, NCH, 8>(P, prm, s);
+}
+
 template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
                                cudaStream_t s) {
-  constexpr int REG = VEC * NCH * (sizeof(typename AccOf<TB>::T) / 4);
-  constexpr int U = REG >= 16 ? 2 : (REG >= 8 ? 4 : 8);
-  auto kern = k_spmm<TV, TB, VEC, NCH, MASKED, U>;
+  if constexpr (!MASKED && VEC * sizeof(TB) >= 4) {
+    if (P->opts.pipeline) return launch_async<TV, TB, VEC, NCH>(P, prm, s);
+  }
+  constexpr int U = Occupancy<VEC, NCH, TB>::U;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm<TV, TB, VEC, NCH, MASKED, U, true>
+                    : k_spmm<TV, TB, VEC, NCH, MASKED, U, false>;
   const int wpc = P->opts.warps_per_cta;
   const int threads = wpc * 32;
-  int64_t grid;
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.chunk_blocks = (q.n_chunk_items + wpc - 1) / wpc;
+  const int64_t n_groups = prm.n_items - q.n_chunk_items;
+  int64_t gblocks = (n_groups + wpc - 1) / wpc;
   if (prm.persistent) {
     int per_sm = 0;
     SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
-    grid = (int64_t)std::max(per_sm, 1) * P->sm_count;
-    grid = std::min<int64_t>(grid, (prm.n_items + wpc - 1) / wpc);
-  } else {
-    grid = (prm.n_items + wpc - 1) / wpc;
+    gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
   }
+  const int64_t grid = q.chunk_blocks + gblocks;
   if (grid <= 0) return SHIRO_OK;
   if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
-  kern<<<(unsigned)grid, threads, 0, s>>>(prm);
+  kern<<<(unsigned)grid, threads, 0, s>>>(q);
   SHIRO_CUDA(cudaGetLastError());
   return SHIRO_OK;
 }

@@ -42,7 +42,8 @@ class shiro_partition(ctypes.Structure):
 
 class shiro_opts(ctypes.Structure):
     _fields_ = [("long_row_nnz", _i32), ("chunk_nnz", _i32), ("group_nnz", _i32),
-                ("group_rows", _i32), ("warps_per_cta", _i32), ("persistent", _i32)]
+                ("group_rows", _i32), ("warps_per_cta", _i32), ("persistent", _i32),
+                ("pipeline", _i32), ("stage_rows", _i32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -202,6 +202,26 @@ shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const
                         int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
                         uint32_t flags, void* scratch, size_t scratch_bytes, void* stream);
 
+/* Allocation-free variant of shiro_spmm.  The paper has no counterpart: it exists for callers that
+ * cannot allocate device memory for the split-row scratch -- code that runs while a stream is
+ * being captured into a CUDA graph (cudaMalloc is not a capturable operation), plug-ins inside
+ * runtimes that hand a kernel only its input and output buffers and own all device memory, and
+ * serving paths that may not allocate after start-up.
+ * Same arguments and results as shiro_spmm without scratch/scratch_bytes: the partial sums of
+ * split rows go to one static device array of SHIRO_NOALLOC_SCRATCH_BYTES (16 MiB) inside the
+ * library, which every GPU that loads the library holds until the process exits.  A plan whose
+ * shiro_spmm_scratch(plan, N, dt) exceeds that size is rejected with
+ * SHIRO_ERR_INSUFFICIENT_WORKSPACE (16 MiB holds 32,768 split-row chunks at N = 128 in FP32).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture begins.  All calls on a device
+ * share the one array, which keeps the last call's partial sums (nothing in it has to start at
+ * zero): calls that overlap on the GPU -- on different streams, or with different plans -- race
+ * and must be serialised by the caller. */
+#define SHIRO_NOALLOC_SCRATCH_BYTES (16 << 20)
+shiro_status shiro_spmm_noalloc(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
+                                int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
+                                uint32_t flags, void* stream);
+
 /* Gradient of C = A B with respect to A's stored values (a sampled dense-dense product on A's
  * pattern): dA[e] = sum_k dC[row(e), k] * Bpack[remap[e], k] (B[col[e], k] for local diagonal
  * tiles).  dC: device M x N of dt (F32/BF16 with F32 dA, or F64 with F64 dA). */

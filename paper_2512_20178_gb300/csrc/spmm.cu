@@ -14,6 +14,7 @@
 //     blocks for column-sorted rows), so C is written once with streaming stores.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 #include "vec.cuh"
@@ -600,3 +601,49 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
 }
 
 }  // extern "C"
+
+// ---- allocation-free SpMM ----
+//
+// Scratch for callers that cannot allocate device memory: one array in the library's own module,
+// created when the module is loaded on a device and kept until the process exits.  Its host-side
+// name is not a device address; the address is looked up once per device below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SHIRO_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" shiro_status shiro_spmm_noalloc(shiro_plan_t plan, const void* Bpack, int64_t ldp,
+                                           const void* B, int64_t ldb, int32_t N,
+                                           shiro_dtype dt, void* C, int64_t ldc, uint32_t flags,
+                                           void* stream) {
+  if (!plan) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  if (N < 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "negative N");
+  int dev = 0;
+  SHIRO_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "device index %d beyond %d", dev, kMaxDevices);
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      SHIRO_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  const size_t need = spmm_scratch_bytes(plan, N, dt);
+  if (need > (size_t)SHIRO_NOALLOC_SCRATCH_BYTES)
+    SHIRO_FAIL(SHIRO_ERR_INSUFFICIENT_WORKSPACE,
+               "shiro_spmm_noalloc: this plan's split rows need %zu bytes of scratch for N=%d, "
+               "more than the %d-byte static scratch; use shiro_spmm with a caller buffer or a "
+               "schedule with larger chunks",
+               need, N, SHIRO_NOALLOC_SCRATCH_BYTES);
+  // The static array needs no clearing: every chunk writes its partial-sum slot before the last
+  // chunk of its row reads the slots back (the arrival counters live in the plan).
+  return launch_spmm(plan, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch,
+                     (size_t)SHIRO_NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream);
+}

@@ -22,6 +22,7 @@ SHIRO_PLAN_LOCAL_DIAG = 0x1
 SHIRO_PLAN_DIAG_ONLY = 0x2
 SHIRO_PLAN_TRANSPOSE = 0x4
 SHIRO_SPMM_ACCUMULATE = 0x1
+SHIRO_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -74,6 +75,7 @@ SIGNATURES = [
     ("shiro_pack", ctypes.c_int, [_vp, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _vp]),
     ("shiro_spmm_scratch", ctypes.c_int, [_vp, _i32, ctypes.c_int, _P(_sz)]),
     ("shiro_spmm", ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _u32, _vp, _sz, _vp]),
+    ("shiro_spmm_noalloc", ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _u32, _vp]),
     ("shiro_sddmm", ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _vp]),
     ("shiro_spmm_backward", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
     ("shiro_batch_workspace", ctypes.c_int, [_i32, _P(shiro_csr), _P(shiro_opts), _P(_sz)]),

@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"],
+                    help="storage of B (and of the packed rows); accumulation is FP32 either way")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time the batched form instead: this many R-MAT graphs, n ~ U{100..20000}, "
+                         "degree log-uniform [4, 40], B n x N in BF16, one CUDA-graph replay per step")
     return ap.parse_args()
 
 
@@ -66,7 +71,7 @@ def workload(args):
 
 
 def config(args, A, extra=None):
-    c = {"workload": f"rmat{args.scale}_deg{args.deg}_N{args.N}_{args.tiles}x{args.tiles}_fp32",
+    c = {"workload": f"rmat{args.scale}_deg{args.deg}_N{args.N}_{args.tiles}x{args.tiles}_{args.dtype}",
          "M": A.M, "K": A.K, "nnz": A.nnz, "N": args.N, "tiles": f"{args.tiles}x{args.tiles}",
          "rmat": [0.57, 0.19, 0.19, 0.05], "seed": args.seed,
          "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
@@ -241,20 +246,27 @@ def run_ours(args):
     rp = torch.from_numpy(A.rowptr).to(dev)
     col = torch.from_numpy(A.col).to(dev)
     val = torch.from_numpy(A.val).to(dev)
-    Bd = torch.from_numpy(B).to(dev)
+    bf16 = args.dtype == "bf16"
+    tdt = torch.bfloat16 if bf16 else torch.float32
+    sz = 2 if bf16 else 4
+    if bf16:
+        Bh = torch.from_numpy(synth.to_bf16_bits(B).view(np.int16)).view(torch.bfloat16)
+    else:
+        Bh = torch.from_numpy(B)
+    Bd = Bh.to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     P = shiro.Plan.create(rp, col, val, A.M, A.K, args.tiles, args.tiles)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     R = P.info.packed_rows
-    Bp = torch.empty((R, N), dtype=torch.float32, device=dev)
+    Bp = torch.empty((R, N), dtype=tdt, device=dev)
     C = torch.empty((A.M, N), dtype=torch.float32, device=dev)
     tuned = None
     if args.autotune:
         P.pack(Bd, out=Bp)
         tuned = P.autotune(Bp, B=Bd, C=C)
-    scratch = P.new_scratch(N, torch.float32)
+    scratch = P.new_scratch(N, tdt)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -286,12 +298,12 @@ def run_ours(args):
     ms = start.elapsed_time(end) / K
     spmm_ms = sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)) / K
     ms_max = reduce_max(ms, world, dev)
-    sp_bytes, pk_bytes = step_bytes(A.M, A.nnz, R, N, 4)
+    sp_bytes, pk_bytes = step_bytes(A.M, A.nnz, R, N, sz)
     value = world * (sp_bytes + pk_bytes) / (ms_max * 1e-3) / 1e9
     gflops = world * 2.0 * A.nnz * N / (ms_max * 1e-3) / 1e9
 
     # End to end through the public API: B from pinned host memory, C back to pinned memory.
-    Bh = torch.from_numpy(B).pin_memory()
+    Bh = Bh.pin_memory()
     Ch = torch.empty((A.M, N), dtype=torch.float32).pin_memory()
     for _ in range(min(args.warmup, 3)):
         Bd.copy_(Bh, non_blocking=True)
@@ -309,7 +321,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = reduce_max(e0.elapsed_time(e1) / Ke, world, dev)
     e2e = {"value": world * (sp_bytes + pk_bytes) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": int(Bh.numel() * 4), "d2h_bytes_per_step": int(Ch.numel() * 4),
+           "h2d_bytes_per_step": int(Bh.numel() * sz), "d2h_bytes_per_step": int(Ch.numel() * 4),
            "ms_per_step": e2e_ms}
 
     peaks = {}
@@ -327,12 +339,13 @@ def run_ours(args):
                 "ms_per_launch": spmm_ms}
 
     forms = None
-    if not args.no_forms:
+    if not args.no_forms and not bf16:
         forms = measure_forms(args, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream)
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "storage": args.dtype,
             "data": "synthetic (seeded R-MAT, counter-based SplitMix64)",
             "config": config(args, A, {"packed_rows": R, "plan_ms": plan_ms,
                                        "schedule": P.info.opts.as_dict(), "autotuned": tuned}),
@@ -392,10 +405,70 @@ def measure_forms(args, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream, 
             "transpose_packed_rows": RT}
 
 
+def run_batch(args):
+    """Batched form: G graphs as one block-diagonal plan; each step replays one CUDA graph that
+    holds the pack and one persistent SpMM launch over every graph."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2512_20178_gb300 import shiro, synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = args.N
+    gb = synth.batch_graphs(args.batch, 5)
+    tens = []
+    for gr in gb.graphs:
+        tens.append((torch.from_numpy(gr.rowptr).to(dev), torch.from_numpy(gr.col).to(dev),
+                     torch.from_numpy(gr.val).to(dev), gr.M, gr.K))
+    t0 = time.perf_counter()
+    P = shiro.Plan.create_batch(tens, opts=shiro.make_opts(persistent=1))
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    M, nnz, R = P.info.M, P.info.nnz, P.info.packed_rows
+    Bh = np.concatenate([synth.dense_normal(gr.K, N, 500 + i) for i, gr in enumerate(gb.graphs)])
+    Bd = torch.from_numpy(synth.to_bf16_bits(Bh).view(np.int16)).to(dev).view(torch.bfloat16)
+    Bp = torch.empty((R, N), dtype=torch.bfloat16, device=dev)
+    C = torch.empty((M, N), dtype=torch.float32, device=dev)
+    scratch = P.new_scratch(N, torch.bfloat16)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            P.pack(Bd, out=Bp)
+            P.spmm(Bp, out=C, scratch=scratch)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        P.pack(Bd, out=Bp)
+        P.spmm(Bp, out=C, scratch=scratch)
+    for _ in range(args.warmup):
+        graph.replay()
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    sp, pk = step_bytes(M, nnz, R, N, 2)
+    print(json.dumps({
+        "metric": METRIC, "value": (sp + pk) / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "bf16",
+        "data": "synthetic (seeded R-MAT graphs)",
+        "config": {"workload": f"batch{args.batch}_rmat_n100-20000_deg4-40_N{N}_bf16_cudagraph",
+                   "graphs": args.batch, "rows": M, "nnz": nnz, "packed_rows": R, "N": N,
+                   "plan_ms": plan_ms, "schedule": P.info.opts.as_dict()},
+        "gflops": 2.0 * nnz * N / (ms * 1e-3) / 1e9, "gpu_launches": 2 * args.steps}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch:
+        run_batch(args)
     else:
         run_ours(args)
 

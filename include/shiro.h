@@ -94,8 +94,10 @@ typedef struct {
   int32_t group_rows;
   int32_t warps_per_cta; /* 1..8 */
   int32_t persistent;    /* 1: grid = SMs x resident CTAs and warps stride over the items */
-  int32_t pipeline;      /* 1: B-row gathers staged through shared memory by asynchronous copies
-                            (two stages per warp); 0: gathers into registers */
+  int32_t pipeline;      /* 0: B-row gathers into registers; 1: staged through shared memory by
+                            per-lane asynchronous copies; 2: staged by one TMA bulk copy per row
+                            (rows of a multiple of 16 bytes, 16-byte aligned; else 1) --
+                            two stages per warp for 1 and 2 */
   int32_t stage_rows;    /* rows per stage with pipeline 1: 8, 16 or 32 (0 = the largest that keeps
                             a stage within 16 KB) */
 } shiro_opts;

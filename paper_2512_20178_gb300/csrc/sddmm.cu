@@ -63,78 +63,117 @@ __device__ __forceinline__ TA transpose_reduce(TA (&part)[32], int lane) {
   return part[0];
 }
 
+// Row of the stream position `pos` (relative to the item start) and the next non-empty row after
+// it: lane l < nr holds the end of row r0 + l in `rel`.
+__device__ __forceinline__ int next_nonempty_row(int rel, bool nonempty, int nr, int pos,
+                                                 int lane) {
+  const unsigned m = __ballot_sync(FULLM, lane < nr && nonempty && rel > pos);
+  return m ? __ffs(m) - 1 : -1;
+}
+
 template <typename TB, int VEC, int NCH, bool MASKED, int U>
-__device__ __forceinline__ void sddmm_item(const SddmmParams<TB>& p, const Item& item, int lane) {
+__device__ __forceinline__ void sddmm_item(const SddmmParams<TB>& p, int32_t* s_idx,
+                                           const Item& item, int lane) {
   using TA = typename AccOf<TB>::T;
   const bool chunk = item.tag <= 0;
   const int32_t r0 = item.row;
-  const int32_t nr = chunk ? 1 : item.tag;
+  const int nr = chunk ? 1 : item.tag;
   const int64_t rp = lane < nr ? __ldg(p.rowptr + r0 + lane + 1) : 0;
-  int64_t e_end = __shfl_sync(FULLM, rp, nr - 1);
-  if (chunk) e_end = min(e_end, item.e0 + (int64_t)p.chunk);
-  int32_t rl = 0;
-  int64_t next = __shfl_sync(FULLM, rp, 0);
-  TA g[NCH][VEC];
-  load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)r0 * p.lddc, p.N, lane, g);
-  for (int64_t e = item.e0; e < e_end; e += 32) {
-    const int n = (int)min((int64_t)32, e_end - e);
-    const int32_t my_idx = lane < n ? __ldcs(p.remap + e + lane) : 0;
+  int rel = (int)(rp - item.e0);
+  const int prev = __shfl_up_sync(FULLM, rel, 1);
+  bool nonempty = lane < nr && rel > (lane ? prev : 0);
+  int total = __shfl_sync(FULLM, rel, nr - 1);
+  if (chunk) {
+    total = min(total, p.chunk);
+    rel = total;
+    nonempty = lane == 0 && total > 0;
+  }
+  // dC slice of the current row and, one row ahead, of the next non-empty row.
+  int cur = next_nonempty_row(rel, nonempty, nr, 0, lane);
+  if (cur < 0) return;
+  int nxt = next_nonempty_row(rel, nonempty, nr, __shfl_sync(FULLM, rel, cur), lane);
+  TA g[NCH][VEC], gn[NCH][VEC];
+  load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + cur) * p.lddc, p.N, lane, g);
+  if (nxt >= 0) load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + nxt) * p.lddc, p.N, lane, gn);
+  int32_t nidx = lane < total ? __ldcs(p.remap + item.e0 + lane) : 0;
+  for (int off = 0; off < total; off += 32) {
+    const int n = min(32, total - off);
+    __syncwarp();
+    s_idx[lane] = nidx;
+    __syncwarp();
+    if (off + 32 + lane < total) nidx = __ldcs(p.remap + item.e0 + off + 32 + lane);
+    const int q = rel - 1 - off;
+    const unsigned bit = (lane < nr && nonempty && q >= 0 && q < 32) ? (1u << q) : 0u;
+    const unsigned endmask = __reduce_or_sync(FULLM, bit);
     TA part[32];
 #pragma unroll
     for (int j = 0; j < 32; j += U) {
       TA b[U][NCH][VEC];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int32_t idx = __shfl_sync(FULLM, my_idx, j + u);
         if (j + u < n) {
-          const TB* row = idx >= 0 ? p.Bpack + (int64_t)idx * p.ldp
-                                   : p.B + (int64_t)(-1 - idx) * p.ldb;
+          const int32_t idx = s_idx[j + u];
+          const TB* row = idx >= 0 ? p.Bpack + (uint64_t)(uint32_t)idx * (uint32_t)p.ldp
+                                   : p.B + (uint64_t)(uint32_t)(-1 - idx) * (uint32_t)p.ldb;
           load_frag<TB, VEC, NCH, MASKED>(row, p.N, lane, b[u]);
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        part[j + u] = 0;
+        TA s = 0;
         if (j + u < n) {
-          const int64_t ee = e + j + u;
-          if (ee >= next && rl < nr - 1) {
-            while (ee >= next && rl < nr - 1) {
-              ++rl;
-              next = __shfl_sync(FULLM, rp, rl);
-            }
-            load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + rl) * p.lddc, p.N, lane, g);
-          }
-          TA s = 0;
 #pragma unroll
           for (int c = 0; c < NCH; ++c)
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) s += g[c][v] * b[u][c][v];
-          part[j + u] = s;
+            for (int v = 0; v < VEC; ++v) s = fma(g[c][v], b[u][c][v], s);
+          if ((endmask >> (j + u)) & 1u) {
+            // The stream leaves row r0 + cur here: move to the prefetched next row.
+            cur = nxt;
+            if (cur >= 0) {
+#pragma unroll
+              for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) g[c][v] = gn[c][v];
+              nxt = next_nonempty_row(rel, nonempty, nr, __shfl_sync(FULLM, rel, cur), lane);
+              if (nxt >= 0)
+                load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + nxt) * p.lddc, p.N, lane, gn);
+            }
+          }
         }
+        part[j + u] = s;
       }
     }
     const TA tot = transpose_reduce<TA>(part, lane);
-    if (lane < n) p.dA[e + lane] = tot;
+    if (lane < n) p.dA[item.e0 + off + lane] = tot;
   }
 }
 
+template <int VEC, int NCH, typename TB>
+struct SddmmOcc {
+  static constexpr int REG = VEC * NCH * (int)(sizeof(typename AccOf<TB>::T) / 4);
+  static constexpr int U = REG >= 16 ? 2 : 4;
+  static constexpr int MIN_BLOCKS = REG <= 4 ? 3 : 2;
+};
+
 template <typename TB, int VEC, int NCH, bool MASKED, int U>
-__global__ void __launch_bounds__(256) k_sddmm(const SddmmParams<TB> p) {
+__global__ void __launch_bounds__(256, (SddmmOcc<VEC, NCH, TB>::MIN_BLOCKS))
+    k_sddmm(const SddmmParams<TB> p) {
+  __shared__ int32_t s_idx[8][32];
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  int64_t it = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5);
+  int64_t it = (int64_t)blockIdx.x * wpb + warp;
   const int64_t step = p.persistent ? (int64_t)gridDim.x * wpb : p.n_items;
   for (; it < p.n_items; it += step) {
     const Item item = p.items[it];
-    sddmm_item<TB, VEC, NCH, MASKED, U>(p, item, lane);
+    sddmm_item<TB, VEC, NCH, MASKED, U>(p, s_idx[warp], item, lane);
   }
 }
 
 template <typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& prm,
                                  cudaStream_t s) {
-  constexpr int REG = VEC * NCH * (sizeof(typename AccOf<TB>::T) / 4);
-  constexpr int U = REG >= 16 ? 2 : (REG >= 8 ? 4 : 8);
+  constexpr int U = SddmmOcc<VEC, NCH, TB>::U;
   const int wpc = std::min(P->opts.warps_per_cta, 8);
   int64_t grid = (prm.n_items + wpc - 1) / wpc;
   if (prm.persistent) grid = std::min<int64_t>(grid, (int64_t)P->sm_count * 8);

@@ -273,6 +273,7 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Bas
 }  // namespace shiro
 
 #include "spmm_async.cuh"
+#include "spmm_bulk.cuh"
 
 namespace shiro {
 
@@ -389,10 +390,67 @@ static shiro_status launch_async(const shiro_plan_s* P, const SpmmParams<TV, TB>
   return launch_async_batch<TV, TB, VEC, NCH, 8>(P, prm, s);
 }
 
+template <typename TV, typename TB, int VEC, int NCH, int BATCH>
+static shiro_status launch_bulk_batch(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                      cudaStream_t s) {
+  using L = BulkLayout<TV, TB, VEC, NCH, BATCH>;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm_bulk<TV, TB, VEC, NCH, BATCH, true>
+                    : k_spmm_bulk<TV, TB, VEC, NCH, BATCH, false>;
+  const int max_smem = 227 * 1024;
+  const int wpc = std::max(1, std::min(P->opts.warps_per_cta, max_smem / L::WARP));
+  const int smem = wpc * L::WARP;
+  SHIRO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.chunk_blocks = (q.n_chunk_items + wpc - 1) / wpc;
+  const int64_t n_groups = prm.n_items - q.n_chunk_items;
+  int64_t gblocks = (n_groups + wpc - 1) / wpc;
+  if (prm.persistent) {
+    int per_sm = 0;
+    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, smem));
+    gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
+  }
+  const int64_t grid = q.chunk_blocks + gblocks;
+  if (grid <= 0) return SHIRO_OK;
+  if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+  kern<<<(unsigned)grid, wpc * 32, smem, s>>>(q);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
+// TMA bulk copies need 16-byte aligned rows whose size is a multiple of 16 bytes.
+template <typename TV, typename TB, int VEC, int NCH>
+static bool bulk_ok(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm) {
+  constexpr int ROW = 32 * VEC * NCH * (int)sizeof(TB);
+  if (ROW % 16 || ROW > 4096) return false;
+  auto al = [](const void* b, int64_t ld) {
+    return ((uintptr_t)b % 16) == 0 && ((uint64_t)ld * sizeof(TB)) % 16 == 0;
+  };
+  if (!al(prm.Bpack, prm.ldp)) return false;
+  if ((P->flags & SHIRO_PLAN_LOCAL_DIAG) && !al(prm.B, prm.ldb)) return false;
+  return true;
+}
+
+template <typename TV, typename TB, int VEC, int NCH>
+static shiro_status launch_bulk(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                cudaStream_t s) {
+  constexpr int ROW = 32 * VEC * NCH * (int)sizeof(TB);
+  int batch = P->opts.stage_rows ? P->opts.stage_rows : 32;
+  while (batch > 8 && batch * ROW > 16384) batch /= 2;
+  if constexpr (32 * ROW <= 16384)
+    if (batch >= 32) return launch_bulk_batch<TV, TB, VEC, NCH, 32>(P, prm, s);
+  if constexpr (16 * ROW <= 16384)
+    if (batch >= 16) return launch_bulk_batch<TV, TB, VEC, NCH, 16>(P, prm, s);
+  return launch_bulk_batch<TV, TB, VEC, NCH, 8>(P, prm, s);
+}
+
 template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
                                cudaStream_t s) {
   if constexpr (!MASKED && VEC * sizeof(TB) >= 4) {
+    if (P->opts.pipeline == 2 && bulk_ok<TV, TB, VEC, NCH>(P, prm))
+      return launch_bulk<TV, TB, VEC, NCH>(P, prm, s);
     if (P->opts.pipeline) return launch_async<TV, TB, VEC, NCH>(P, prm, s);
   }
   constexpr int U = Occupancy<VEC, NCH, TB>::U;
@@ -540,22 +598,24 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
   // size, the largest rows decide whether splitting matters at all.
   const double avg = P->M ? (double)P->nnz / (double)P->M : 0.0;
   std::vector<shiro_opts> cands;
-  const int32_t groups[] = {32, 64, 128, 256};
+  const int32_t groups[] = {128, 256, 512, 1024};
   const int32_t chunks[] = {256, 512, 1024};
-  const int32_t warps[] = {4, 8};
+  const int32_t warps[] = {1, 2, 4};
   for (int32_t gn : groups) {
     if (gn < avg / 2) continue;
     for (int32_t ch : chunks) {
       if (P->max_row_nnz <= ch && ch != 512) continue;
       for (int32_t w : warps) {
-        for (int32_t pers = 0; pers < 2; ++pers) {
+        for (int32_t pipe = 0; pipe < 2; ++pipe) {
           shiro_opts o = start;
           o.group_nnz = gn;
           o.group_rows = 32;
           o.chunk_nnz = ch;
           o.long_row_nnz = 2 * ch;
           o.warps_per_cta = w;
-          o.persistent = pers;
+          o.persistent = 0;
+          o.pipeline = pipe;
+          o.stage_rows = 16;
           cands.push_back(o);
         }
       }

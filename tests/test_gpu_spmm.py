@@ -150,3 +150,54 @@ def test_full_size_rmat20_sampled_rows(rmat20):
     src = P.export()["pack_src"].cpu().numpy()
     pick = np.unique((synth.uniform_f64(10, synth.STREAM_PERM, 0, 4000) * len(src)).astype(np.int64))
     assert np.array_equal(Bp[torch.from_numpy(pick).to(gu.dev())].cpu().numpy(), B[src[pick]])
+
+
+@pytest.mark.parametrize("case", ["f32_n128", "f32_n256", "f32_n64", "f32_n32", "bf16_n128",
+                                  "bf16_n256", "f64_n128", "local_diag", "accumulate", "hub"])
+def test_pipelines_bit_identical(case):
+    """Register gathers, per-lane async copies and TMA bulk copies sum every row in the same
+    order, so the three pipelines give bit-identical C (and each passes the oracle bound)."""
+    shiro = gu.lib()
+    flags, vdt, dt, acc = 0, torch.float32, torch.float32, False
+    A, N = synth.rmat(13, 12, 131), 128
+    if case == "f32_n256":
+        N = 256
+    elif case == "f32_n64":
+        N = 64
+    elif case == "f32_n32":
+        N = 32
+    elif case.startswith("bf16"):
+        dt = torch.bfloat16
+        N = 256 if case.endswith("256") else 128
+    elif case == "f64_n128":
+        vdt, dt = torch.float64, torch.float64
+    elif case == "local_diag":
+        flags = shiro.SHIRO_PLAN_LOCAL_DIAG
+    elif case == "accumulate":
+        acc = True
+    elif case == "hub":
+        A = synth.hub_matrix(64, 1 << 16, 5, 1 << 16, 2, 132)
+    B = synth.dense_normal(A.K, N, 133)
+    if dt == torch.bfloat16:
+        bits = synth.to_bf16_bits(B)
+        B = synth.bf16_bits_to_f32(bits).reshape(B.shape)
+        Bd = torch.from_numpy(bits.view(np.int16)).to(gu.dev()).view(torch.bfloat16)
+    else:
+        Bd = torch.from_numpy(B).to(gu.dev()).to(dt)
+    outs = []
+    for pipe in (0, 1, 2):
+        opts = shiro.make_opts(pipeline=pipe, long_row_nnz=128, chunk_nnz=64, group_nnz=256,
+                               warps_per_cta=2)
+        P = gu.plan_of(A, 4, 4, flags, opts=opts, vdt=vdt)
+        Bp = P.pack(Bd)
+        C = P.spmm(Bp, B=Bd)
+        if acc:
+            P.spmm(Bp, B=Bd, out=C, accumulate=True)
+        P.check()
+        torch.cuda.synchronize()
+        outs.append(C.cpu())
+    assert torch.equal(outs[0], outs[1]), "async pipeline differs from register gathers"
+    assert torch.equal(outs[0], outs[2]), "bulk pipeline differs from register gathers"
+    C = outs[0].numpy() / (2.0 if acc else 1.0)
+    err = gu.scaled_err(C, oracle.spmm(A, B), oracle.abs_scale(A, B))
+    assert err <= gu.TOL, err

@@ -596,7 +596,7 @@ void shiro_default_opts(shiro_opts* o) {
   o->chunk_nnz = 512;
   o->group_nnz = 512;
   o->group_rows = 32;
-  o->warps_per_cta = 2;
+  o->warps_per_cta = 1;
   o->persistent = 0;
   o->pipeline = 0;
   o->stage_rows = 0;

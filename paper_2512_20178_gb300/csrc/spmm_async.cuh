@@ -76,25 +76,32 @@ __device__ __forceinline__ void spmm_span_async(const SpmmParams<TV, TB>& p, cha
     pr.idx = nidx;
     pr.val = nval;
     if (lane < BATCH) pairs[s * 32 + lane] = pr;
-    __syncwarp();
+    const int32_t my_idx = nidx;
     const int nxt = off + BATCH + lane;
     if (lane < BATCH && nxt < total) {
       nidx = __ldcs(p.remap + base + nxt);
       nval = __ldcs(p.val + base + nxt);
     }
+    // Row indices come from the lanes' registers by shuffle, fully unrolled, so the copies of a
+    // batch issue back to back instead of one dependent index read per row.
     const uint32_t dst0 = s_stage + s * L::STAGE + lane * L::PIECE;
-    for (int j = 0; j < n; ++j) {
-      const int32_t idx = pairs[s * 32 + j].idx;
-      const TB* row;
-      if (LOCAL && idx < 0)
-        row = p.B + (uint64_t)(uint32_t)(-1 - idx) * (uint32_t)p.ldb;
-      else
-        row = p.Bpack + (uint64_t)(uint32_t)idx * (uint32_t)p.ldp;
 #pragma unroll
-      for (int c = 0; c < NCH; ++c)
-        cp_async<L::PIECE>(dst0 + j * L::ROW + c * 32 * L::PIECE, row + c * 32 * VEC + lane * VEC);
+    for (int j = 0; j < BATCH; ++j) {
+      const int32_t idx = __shfl_sync(0xffffffffu, my_idx, j);
+      if (j < n) {
+        const TB* row;
+        if (LOCAL && idx < 0)
+          row = p.B + (uint64_t)(uint32_t)(-1 - idx) * (uint32_t)p.ldb;
+        else
+          row = p.Bpack + (uint64_t)(uint32_t)idx * (uint32_t)p.ldp;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+          cp_async<L::PIECE>(dst0 + j * L::ROW + c * 32 * L::PIECE,
+                             row + c * 32 * VEC + lane * VEC);
+      }
     }
     cp_async_commit();
+    __syncwarp();
   };
 
   if (nb > 0) issue(0);

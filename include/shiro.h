@@ -97,7 +97,9 @@ typedef struct {
   int32_t pipeline;      /* 0: B-row gathers into registers; 1: staged through shared memory by
                             per-lane asynchronous copies; 2: staged by one TMA bulk copy per row
                             (rows of a multiple of 16 bytes, 16-byte aligned; else 1) --
-                            two stages per warp for 1 and 2 */
+                            two stages per warp for 1 and 2; 3: rows of 128 or 256 bytes (FP32
+                            N = 32/64, BF16 N = 64/128) split across 4 or 2 lane groups that take
+                            interleaved nonzeros of a row (other rows as 0) */
   int32_t stage_rows;    /* rows per stage with pipeline 1: 8, 16 or 32 (0 = the largest that keeps
                             a stage within 16 KB) */
 } shiro_opts;
@@ -255,8 +257,10 @@ shiro_status shiro_batch_plan_create(int32_t G, const shiro_csr* graphs, const s
 
 /* Autotuner: times shiro_spmm over a set of candidate schedules on the caller's operands (Bpack,
  * C and scratch as for shiro_spmm; C is overwritten) and leaves the fastest one in the plan
- * (*best receives it).  Candidates are chosen from N and the plan's degree profile and are
- * limited to those whose scratch fits scratch_bytes.  Synchronises `stream`. */
+ * (*best receives it).  Candidates vary the row-group size (from the average row length), the
+ * chunk size of long rows (only when some row is longer), the CTA size and, for rows of 128 or
+ * 256 bytes, the lane-group pipeline; the persistent mode stays as set.  Candidates whose scratch
+ * does not fit scratch_bytes are skipped.  Synchronises `stream`. */
 shiro_status shiro_autotune(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
                             int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
                             void* scratch, size_t scratch_bytes, int32_t reps, void* stream,

@@ -151,8 +151,17 @@ __device__ __forceinline__ void sddmm_item(const SddmmParams<TB>& p, int32_t* s_
 template <int VEC, int NCH, typename TB>
 struct SddmmOcc {
   static constexpr int REG = VEC * NCH * (int)(sizeof(typename AccOf<TB>::T) / 4);
+#ifdef SHIRO_SDDMM_U
+  static constexpr int U = REG >= 16 ? 2 : SHIRO_SDDMM_U;
+#else
   static constexpr int U = REG >= 16 ? 2 : 4;
-  static constexpr int MIN_BLOCKS = REG <= 4 ? 3 : 2;
+#endif
+  // 64 registers (32 warps per SM) measured faster than 80, despite a few spilled bytes.
+#ifdef SHIRO_SDDMM_MIN_BLOCKS
+  static constexpr int MIN_BLOCKS = REG <= 4 ? SHIRO_SDDMM_MIN_BLOCKS : 2;
+#else
+  static constexpr int MIN_BLOCKS = REG <= 4 ? 4 : 2;
+#endif
 };
 
 template <typename TB, int VEC, int NCH, bool MASKED, int U>

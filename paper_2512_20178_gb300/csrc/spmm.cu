@@ -274,6 +274,7 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Bas
 
 #include "spmm_async.cuh"
 #include "spmm_bulk.cuh"
+#include "spmm_grouped.cuh"
 
 namespace shiro {
 
@@ -429,6 +430,32 @@ static shiro_status launch_bulk_batch(const shiro_plan_s* P, const SpmmParams<TV
   return SHIRO_OK;
 }
 
+template <typename TV, typename TB, int G>
+static shiro_status launch_grouped(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                   cudaStream_t s) {
+  constexpr int VEC = 16 / (int)sizeof(TB);
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm_grouped<TV, TB, VEC, G, 4, true>
+                    : k_spmm_grouped<TV, TB, VEC, G, 4, false>;
+  const int wpc = P->opts.warps_per_cta;
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.chunk_blocks = (q.n_chunk_items + wpc - 1) / wpc;
+  const int64_t n_groups = prm.n_items - q.n_chunk_items;
+  int64_t gblocks = (n_groups + wpc - 1) / wpc;
+  if (prm.persistent) {
+    int per_sm = 0;
+    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, 0));
+    gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
+  }
+  const int64_t grid = q.chunk_blocks + gblocks;
+  if (grid <= 0) return SHIRO_OK;
+  if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+  kern<<<(unsigned)grid, wpc * 32, 0, s>>>(q);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
 // TMA bulk copies need 16-byte aligned rows whose size is a multiple of 16 bytes.
 template <typename TV, typename TB, int VEC, int NCH>
 static bool bulk_ok(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm) {
@@ -546,6 +573,14 @@ static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t
     if (local) r = r && aligned(B, ldb, esz, vec);
     return r;
   };
+  if constexpr (!std::is_same<TB, double>::value) {
+    // Narrow rows (128 or 256 bytes) split across lane groups (pipeline 3).
+    const int64_t row_bytes = (int64_t)N * (int64_t)esz;
+    if (P->opts.pipeline == 3 && (row_bytes == 128 || row_bytes == 256) && ok((int)(16 / esz))) {
+      if (row_bytes == 128) return launch_grouped<TV, TB, 4>(P, prm, s);
+      return launch_grouped<TV, TB, 2>(P, prm, s);
+    }
+  }
   const int v16 = (int)(16 / esz);
   const Variant v = pick_variant(dt, N, ok(v16), ok(v16 / 2 ? v16 / 2 : 1), ok(v16 / 4 ? v16 / 4 : 1));
   if (!v.vec) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "N=%d beyond the supported 512 columns", N);
@@ -611,21 +646,24 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
   const int32_t groups[] = {128, 256, 512, 1024};
   const int32_t chunks[] = {256, 512, 1024};
   const int32_t warps[] = {1, 2, 4};
+  // Pipelines worth trying: register gathers, and lane groups when rows are 128 or 256 bytes.
+  const int64_t row_bytes = (int64_t)N * (int64_t)dtype_size(dt);
+  const bool narrow = dt != SHIRO_F64 && (row_bytes == 128 || row_bytes == 256);
+  const int32_t pipes[] = {0, 3};
   for (int32_t gn : groups) {
     if (gn < avg / 2) continue;
     for (int32_t ch : chunks) {
       if (P->max_row_nnz <= ch && ch != 512) continue;
       for (int32_t w : warps) {
-        for (int32_t pipe = 0; pipe < 2; ++pipe) {
+        for (int32_t pipe : pipes) {
+          if (pipe == 3 && !narrow) continue;
           shiro_opts o = start;
           o.group_nnz = gn;
           o.group_rows = 32;
           o.chunk_nnz = ch;
           o.long_row_nnz = 2 * ch;
           o.warps_per_cta = w;
-          o.persistent = 0;
-          o.pipeline = pipe;
-          o.stage_rows = 16;
+          o.pipeline = pipe;  // persistent mode stays as the caller set it
           cands.push_back(o);
         }
       }

@@ -201,3 +201,47 @@ def test_pipelines_bit_identical(case):
     C = outs[0].numpy() / (2.0 if acc else 1.0)
     err = gu.scaled_err(C, oracle.spmm(A, B), oracle.abs_scale(A, B))
     assert err <= gu.TOL, err
+
+
+@pytest.mark.parametrize("case", ["f32_n32", "f32_n64", "bf16_n64", "bf16_n128", "local_diag",
+                                  "accumulate", "hub", "empty_rows", "persistent"])
+def test_grouped_pipeline(case):
+    """Narrow rows split across lane groups (pipeline 3): within the oracle bound, deterministic."""
+    shiro = gu.lib()
+    flags, dt, acc, N, pers = 0, torch.float32, False, 64, 0
+    A = synth.rmat(13, 12, 141)
+    if case == "f32_n32":
+        N = 32
+    elif case.startswith("bf16"):
+        dt = torch.bfloat16
+        N = 64 if case.endswith("64") else 128
+    elif case == "local_diag":
+        flags = shiro.SHIRO_PLAN_LOCAL_DIAG
+    elif case == "accumulate":
+        acc = True
+    elif case == "hub":
+        A = synth.hub_matrix(64, 1 << 16, 5, 1 << 16, 2, 142)
+    elif case == "empty_rows":
+        A = synth.random_small(300, 300, 0.02, 143, empty_rows=150)
+    elif case == "persistent":
+        pers = 1
+    B = synth.dense_normal(A.K, N, 144)
+    if dt == torch.bfloat16:
+        bits = synth.to_bf16_bits(B)
+        B = synth.bf16_bits_to_f32(bits).reshape(B.shape)
+        Bd = torch.from_numpy(bits.view(np.int16)).to(gu.dev()).view(torch.bfloat16)
+    else:
+        Bd = torch.from_numpy(B).to(gu.dev())
+    opts = shiro.make_opts(pipeline=3, long_row_nnz=128, chunk_nnz=64, persistent=pers)
+    P = gu.plan_of(A, 4, 4, flags, opts=opts)
+    Bp = P.pack(Bd)
+    C = P.spmm(Bp, B=Bd)
+    C2 = P.spmm(Bp, B=Bd)
+    if acc:
+        P.spmm(Bp, B=Bd, out=C, accumulate=True)
+    P.check()
+    torch.cuda.synchronize()
+    assert torch.equal(C2 * (2 if acc else 1), C), "grouped SpMM not deterministic"
+    Ch = C.cpu().numpy() / (2.0 if acc else 1.0)
+    err = gu.scaled_err(Ch, oracle.spmm(A, B), oracle.abs_scale(A, B))
+    assert err <= gu.TOL, err

@@ -23,10 +23,53 @@ stand-ins reproduce their shape: square, power-law degree, ~half the ids empty a
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
+import subprocess
 from dataclasses import dataclass
 
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_GEN_SRC = os.path.join(_HERE, "synth_gen.c")
+_GEN_LIB = os.path.join(_HERE, "libsynthgen.so")
+_gen = None
+
+
+def build_gen(force: bool = False) -> str:
+    """Compile synth_gen.c (the multi-threaded generators) next to this file."""
+    if not force and os.path.exists(_GEN_LIB) and os.path.getmtime(_GEN_LIB) >= os.path.getmtime(_GEN_SRC):
+        return _GEN_LIB
+    tmp = _GEN_LIB + f".{os.getpid()}.tmp"
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _GEN_SRC, "-o", tmp]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + ["-lm"], check=True)
+    os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _lib():
+    global _gen
+    if _gen is None:
+        build_gen()
+        L = ctypes.CDLL(_GEN_LIB)
+        u64, i64, i32, vp = ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+        L.synth_normal_f32.argtypes = [u64, u64, i64, ctypes.c_double, vp]
+        L.synth_uniform_f32.argtypes = [u64, u64, i64, i64, vp]
+        L.synth_rmat_keys.argtypes = [u64, u64, i32, i64, i64, i64, u64, u64, u64, vp]
+        L.synth_keys_to_csr.argtypes = [vp, i64, i64, vp, vp]
+        L.synth_keys_to_csr.restype = i64
+        L.synth_f32_to_bf16.argtypes = [vp, i64, vp]
+        _gen = L
+    return _gen
+
+
+def _vp(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
 
 GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -85,27 +128,18 @@ def uniform_f64(seed: int, stream: int, start: int, count: int) -> np.ndarray:
 
 def uniform_f32(seed: int, stream: int, start: int, count: int) -> np.ndarray:
     """U[0,1) floats from the top 24 bits (exactly representable in FP32)."""
-    return ((draw_bits(seed, stream, start, count) >> np.uint64(40)).astype(np.float32)
-            * np.float32(2.0 ** -24))
+    out = np.empty(count, dtype=np.float32)
+    if count:
+        _lib().synth_uniform_f32(seed, stream, start, count, _vp(out))
+    return out
 
 
 def normal_f32(seed: int, stream: int, count: int, std: float = 1.0) -> np.ndarray:
-    """N(0, std^2) FP32 values by the Box-Muller transform, two outputs per 64-bit draw."""
+    """N(0, std^2) FP32 values by the Box-Muller transform, two outputs per 64-bit draw:
+    draw k gives outputs 2k and 2k + 1 from u1 = (hi32 + 1/2) 2^-32 and u2 = (lo32 + 1/2) 2^-32."""
     out = np.empty(count, dtype=np.float32)
-    pairs = (count + 1) // 2
-    for s in range(0, pairs, _CHUNK):
-        n = min(_CHUNK, pairs - s)
-        z = draw_bits(seed, stream, s, n)
-        u1 = ((z >> np.uint64(32)).astype(np.float64) + 0.5) * (2.0 ** -32)
-        u2 = ((z & _MASK32).astype(np.float64) + 0.5) * (2.0 ** -32)
-        r = np.sqrt(-2.0 * np.log(u1)) * std
-        t = 2.0 * np.pi * u2
-        v = np.empty(2 * n, dtype=np.float64)
-        v[0::2] = r * np.cos(t)
-        v[1::2] = r * np.sin(t)
-        lo = 2 * s
-        hi = min(count, lo + 2 * n)
-        out[lo:hi] = v[: hi - lo]
+    if count:
+        _lib().synth_normal_f32(seed, stream, count, float(std), _vp(out))
     return out
 
 
@@ -119,9 +153,11 @@ def to_bf16_bits(x: np.ndarray) -> np.ndarray:
     """Round FP32 to BF16 (round to nearest, ties to even); returns the uint16 bit patterns.
 
     Inputs are finite; NaN handling is not needed for these generators."""
-    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    b = b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))
-    return (b >> np.uint64(16)).astype(np.uint16)
+    src = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(src.shape, dtype=np.uint16)
+    if src.size:
+        _lib().synth_f32_to_bf16(_vp(src), src.size, _vp(out))
+    return out
 
 
 def bf16_bits_to_f32(h: np.ndarray) -> np.ndarray:
@@ -169,38 +205,41 @@ def er(n: int, avg_deg: float, seed: int, lo: float = -1.0, hi: float = 1.0) -> 
     return csr_from_sorted_keys(k, n, n, val)
 
 
-def rmat_keys(n: int, scale: int, samples: int, seed: int,
-              a: float = 0.57, b: float = 0.19, c: float = 0.19) -> np.ndarray:
-    """Sorted unique (row * n + col) keys of an R-MAT pattern with duplicates merged.
+def keys_to_pattern(keys: np.ndarray, n: int):
+    """(rowptr, col) of the distinct keys row * n + col (negative keys skipped), columns ascending."""
+    keys = np.ascontiguousarray(keys, dtype=np.int64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.empty(max(1, len(keys)), dtype=np.int32)
+    nnz = _lib().synth_keys_to_csr(_vp(keys), len(keys), n, _vp(rowptr), _vp(col))
+    return rowptr, col[:nnz].copy()
+
+
+def rmat_samples(n: int, scale: int, samples: int, seed: int,
+                 a: float = 0.57, b: float = 0.19, c: float = 0.19) -> np.ndarray:
+    """Keys row * n + col of R-MAT edge samples (not deduplicated; -1 for rejected samples).
 
     Each sample descends ``scale`` levels, most significant bit first; at every level one
     32-bit uniform picks the quadrant (a: top-left, b: top-right, c: bottom-left, d: bottom-right).
     Samples with an endpoint >= n are rejected (only when n is not a power of two)."""
-    ta = np.uint64(int(a * 2 ** 32))
-    tab = np.uint64(int((a + b) * 2 ** 32))
-    tabc = np.uint64(int((a + b + c) * 2 ** 32))
-    out = []
-    for s in range(0, samples, _CHUNK):
-        cnt = min(_CHUNK, samples - s)
-        r = np.zeros(cnt, dtype=np.int64)
-        cc = np.zeros(cnt, dtype=np.int64)
-        for l2 in range((scale + 1) // 2):
-            z = draw_bits(seed, STREAM_RMAT + l2, s, cnt)
-            for half in (0, 1):
-                lvl = 2 * l2 + half
-                if lvl >= scale:
-                    break
-                u = (z >> np.uint64(32)) if half == 0 else (z & _MASK32)
-                rb = (u >= tab).astype(np.int64)
-                cb = (((u >= ta) & (u < tab)) | (u >= tabc)).astype(np.int64)
-                sh = scale - 1 - lvl
-                r |= rb << sh
-                cc |= cb << sh
-        if (1 << scale) != n:
-            keep = (r < n) & (cc < n)
-            r, cc = r[keep], cc[keep]
-        out.append(sorted_unique(r * n + cc))
-    return sorted_unique(np.concatenate(out)) if len(out) > 1 else out[0]
+    ta, tab, tabc = int(a * 2 ** 32), int((a + b) * 2 ** 32), int((a + b + c) * 2 ** 32)
+    keys = np.empty(max(1, samples), dtype=np.int64)
+    if samples:
+        _lib().synth_rmat_keys(seed, STREAM_RMAT, scale, n, 0, samples, ta, tab, tabc, _vp(keys))
+    return keys[:samples]
+
+
+def rmat_pattern(n: int, scale: int, samples: int, seed: int, a: float = 0.57, b: float = 0.19,
+                 c: float = 0.19):
+    """(rowptr, col) of an R-MAT pattern with duplicates merged."""
+    return keys_to_pattern(rmat_samples(n, scale, samples, seed, a, b, c), n)
+
+
+def rmat_keys(n: int, scale: int, samples: int, seed: int,
+              a: float = 0.57, b: float = 0.19, c: float = 0.19) -> np.ndarray:
+    """Sorted unique (row * n + col) keys of an R-MAT pattern with duplicates merged."""
+    rowptr, col = rmat_pattern(n, scale, samples, seed, a, b, c)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    return rows * n + col.astype(np.int64)
 
 
 def rmat(scale: int, avg_deg: int, seed: int, n: int | None = None,
@@ -208,10 +247,10 @@ def rmat(scale: int, avg_deg: int, seed: int, n: int | None = None,
          lo: float = 0.0, hi: float = 1.0) -> CSR:
     """R-MAT CSR with avg_deg * n samples, duplicates merged, values U(lo, hi) in CSR order."""
     n = (1 << scale) if n is None else n
-    keys = rmat_keys(n, scale, avg_deg * n, seed, a, b, c)
-    u = uniform_f32(seed, STREAM_VAL, 0, len(keys))
+    rowptr, col = rmat_pattern(n, scale, avg_deg * n, seed, a, b, c)
+    u = uniform_f32(seed, STREAM_VAL, 0, len(col))
     val = (np.float32(lo) + np.float32(hi - lo) * u).astype(np.float32)
-    return csr_from_sorted_keys(keys, n, n, val)
+    return CSR(n, n, rowptr, col, val)
 
 
 def gcn_normalized(scale: int, avg_deg: int, seed: int) -> CSR:
@@ -220,15 +259,15 @@ def gcn_normalized(scale: int, avg_deg: int, seed: int) -> CSR:
     Built from a binary R-MAT pattern; the value of (i, j) is 1/sqrt(d_i d_j) computed in FP64
     and stored in FP32, d being the row count of the symmetrised pattern including the loop."""
     n = 1 << scale
-    k = rmat_keys(n, scale, avg_deg * n, seed)
+    k = rmat_samples(n, scale, avg_deg * n, seed)
+    k = k[k >= 0]
     r, c = k // n, k % n
     diag = np.arange(n, dtype=np.int64)
-    keys = sorted_unique(np.concatenate([k, c * n + r, diag * n + diag]))
-    rows = keys // n
-    cols = keys - rows * n
-    d = np.bincount(rows, minlength=n).astype(np.float64)
-    val = (1.0 / np.sqrt(d[rows] * d[cols])).astype(np.float32)
-    return csr_from_sorted_keys(keys, n, n, val)
+    rowptr, col = keys_to_pattern(np.concatenate([k, c * n + r, diag * n + diag]), n)
+    d = np.diff(rowptr).astype(np.float64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    val = (1.0 / np.sqrt(d[rows] * d[col])).astype(np.float32)
+    return CSR(n, n, rowptr, col, val)
 
 
 def induced_subgraph(A: CSR, n_sub: int) -> CSR:
@@ -266,9 +305,9 @@ def batch_graphs(G: int, seed: int, n_lo: int = 100, n_hi: int = 20000,
         scale = max(1, int(math.ceil(math.log2(n))))
         samples = int(round(ds[g] * n))
         sub_seed = seed * 1000003 + g
-        keys = rmat_keys(n, scale, samples, sub_seed)
-        val = uniform_f32(sub_seed, STREAM_VAL, 0, len(keys))
-        graphs.append(csr_from_sorted_keys(keys, n, n, val))
+        rowptr, col = rmat_pattern(n, scale, samples, sub_seed)
+        val = uniform_f32(sub_seed, STREAM_VAL, 0, len(col))
+        graphs.append(CSR(n, n, rowptr, col, val))
     return GraphBatch(graphs, ns, ds)
 
 

@@ -97,3 +97,29 @@ def check_spmm(A, B_host, C_dev, rows=None, tol=TOL):
     err = scaled_err(C, C64, S)
     assert err <= tol, f"scaled error {err:.3e} > {tol}"
     return err
+
+
+def sampled_rows_error(A, B_host, C_rows, rows):
+    """Per-row maximum scaled error of C_rows (GPU rows `rows` of C) against the FP64 oracle, on a
+    sub-problem holding only those rows and the B rows they touch (so a large B is never
+    converted to FP64 whole)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    lens = np.diff(A.rowptr)[rows]
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    idx = np.concatenate([np.arange(A.rowptr[r], A.rowptr[r + 1]) for r in rows]) \
+        if rp[-1] else np.zeros(0, np.int64)
+    cols = A.col[idx]
+    ucols, local = np.unique(cols, return_inverse=True)
+    S = synth.CSR(len(rows), max(1, len(ucols)), rp, local.astype(np.int32), A.val[idx])
+    Bs = np.asarray(B_host[ucols]) if len(ucols) else np.zeros((1, B_host.shape[1]), np.float32)
+    C64 = oracle.spmm(S, Bs)
+    Sc = oracle.abs_scale(S, Bs)
+    C = np.asarray(C_rows, dtype=np.float64)
+    d = np.abs(C - C64)
+    zero = Sc == 0
+    if np.any(d[zero] != 0):
+        return np.full(len(rows), np.inf)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(zero, 0.0, d / np.where(zero, 1.0, Sc))
+    return r.max(axis=1) if r.size else np.zeros(len(rows))

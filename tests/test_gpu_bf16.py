@@ -52,3 +52,37 @@ def test_bf16_rmat18_deg32_n256():
     rows = np.unique(np.concatenate([(synth.uniform_f64(5, synth.STREAM_PERM, 0, 2000) * A.M).astype(np.int64),
                                      np.argsort(deg)[-32:]]))
     gu.check_spmm(A, Bq, C, rows=rows)
+
+
+def test_full_size_precision_rmat22_deg32_n256():
+    """The precision workload at full size: R-MAT 2^22, avg degree 32, FP32 values U(0,1), B
+    2^22 x 256 stored in BF16, FP32 accumulation and C, 4x4 tiles.  Sampled rows (random, the 64
+    longest, empty ones) against the FP64 oracle on the BF16-rounded B; the per-row maximum scaled
+    error is reported, and the quantisation error against the FP32 B."""
+    A = synth.rmat(22, 32, 3)
+    B = synth.dense_normal(A.K, 256, 3)
+    bits = synth.to_bf16_bits(B)
+    P = gu.plan_of(A, 4, 4)
+    d = gu.dev()
+    Bd = torch.from_numpy(bits.view(np.int16)).to(d).view(torch.bfloat16)
+    C = P.spmm(P.pack(Bd))
+    torch.cuda.synchronize()
+    deg = np.diff(A.rowptr)
+    rows = np.unique(np.concatenate([
+        (synth.uniform_f64(7, synth.STREAM_PERM, 0, 1500) * A.M).astype(np.int64),
+        np.argsort(deg)[-64:], np.nonzero(deg == 0)[0][:32]]))
+    Cr = C[torch.from_numpy(rows).to(d)].cpu().numpy()
+    Bq_rows = lambda ix: synth.bf16_bits_to_f32(bits[ix]).reshape(len(ix), -1)
+
+    class _View:  # rows of the BF16-rounded B on demand (the full FP32 copy would be 4 GB more)
+        shape = B.shape
+        def __getitem__(self, ix):
+            return Bq_rows(ix)
+
+    err = gu.sampled_rows_error(A, _View(), Cr, rows)
+    q = gu.sampled_rows_error(A, B, Cr, rows)
+    print(f"precision workload: nnz={A.nnz}, rows checked={len(rows)}, per-row max scaled error "
+          f"vs FP64 on the BF16 B: max {err.max():.2e} median {np.median(err):.2e}; vs FP64 on the "
+          f"FP32 B (quantisation): max {q.max():.2e} median {np.median(q):.2e}")
+    assert err.max() <= gu.TOL
+    assert q.max() <= 2 ** -8

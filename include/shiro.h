@@ -156,6 +156,37 @@ shiro_status shiro_plan_tile_stats(shiro_plan_t plan, int64_t* tile_nnz, int64_t
 shiro_status shiro_plan_volumes(shiro_plan_t plan, int32_t N, shiro_dtype dt, int64_t* v_block,
                                 int64_t* v_col, int64_t* v_row);
 
+/* Joint row-column strategy (Sec. 5.2-5.3) for every tile: a minimum vertex cover of the bipartite
+ * graph rows--columns whose edges are the tile's nonzeros (uniform costs, Sec. 5.4: the cover size
+ * mu equals the maximum matching by Koenig's theorem; Hopcroft-Karp finds it and the cover is read
+ * off the alternating reachability from unmatched rows).  Outputs (host arrays, any may be NULL):
+ * tile_mu, tile_cover_rows, tile_cover_cols (n_tiles entries; mu = rows + columns of the cover,
+ * V_joint = mu * N * sz, Eq. 9) and nnz_row_based (nnz bytes: 0 if the nonzero's column is in the
+ * cover -- its B row is sent, Eq. 2 --, 1 if only its row is -- a partial C row is sent, Eq. 3).
+ * Diagonal tiles of a LOCAL_DIAG plan communicate nothing and report 0.  Offline host work (tiles
+ * in parallel threads); synchronises `stream`. */
+shiro_status shiro_plan_joint(shiro_plan_t plan, int64_t* tile_mu, int64_t* tile_cover_rows,
+                              int64_t* tile_cover_cols, uint8_t* nnz_row_based, void* stream);
+
+/* Split of A by a joint cover (nnz_row_based from shiro_plan_joint, host, nnz bytes) into the
+ * three CSR matrices whose SpMMs compute C = A B the joint way (Sec. 5.1 stages 3 and 5):
+ *   A_col (M x K): the column-based nonzeros, to be planned on the same grid -- its tiles' Cols are
+ *     the cover columns, so packing B for it sends exactly the cover's B rows (Eq. 2 part of Eq. 9);
+ *   A_rs (split_rows x K): one row per (tile, cover row) pair, tiles in order, holding that row's
+ *     row-based nonzeros of the tile; A_rs B is the packed buffer of partial C rows the owners of B
+ *     would send (Eq. 3 part of Eq. 9); plan it 1 x 1 with LOCAL_DIAG so it reads B in place;
+ *   A_agg (M x split_rows): 0/1 rows adding each partial row to its C row in tile order (stage 5);
+ *     plan it 1 x 1 with LOCAL_DIAG and run its SpMM with SHIRO_SPMM_ACCUMULATE over the partials.
+ * shiro_joint_split_sizes gives col_nnz, split_rows and split_nnz; shiro_joint_split fills caller
+ * device buffers: col_* (M+1, col_nnz, col_nnz), rs_* (split_rows+1, split_nnz, split_nnz), agg_*
+ * (M+1, split_rows, split_rows); values in the plan's vdt.  Host work; synchronises `stream`. */
+shiro_status shiro_joint_split_sizes(shiro_plan_t plan, const uint8_t* nnz_row_based,
+                                     int64_t* col_nnz, int64_t* split_rows, int64_t* split_nnz);
+shiro_status shiro_joint_split(shiro_plan_t plan, const uint8_t* nnz_row_based,
+                               int64_t* col_rowptr, int32_t* col_col, void* col_val,
+                               int64_t* rs_rowptr, int32_t* rs_col, void* rs_val,
+                               int64_t* agg_rowptr, int32_t* agg_col, void* agg_val, void* stream);
+
 /* Copies the plan's index arrays into caller device buffers (any may be NULL):
  * cols_sorted (total_cols): Cols of every tile, ascending, concatenated in tile order;
  * pack_src (packed_rows): the B row gathered into each packed row;

@@ -239,6 +239,33 @@ def transpose(A):
     return rowptrT, colT[: A.nnz].copy(), perm[: A.nnz].copy()
 
 
+def max_matching(nL: int, nR: int, ptr, adj) -> int:
+    """Maximum matching of a bipartite graph (= minimum vertex cover size, Koenig)."""
+    ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+    adj = np.ascontiguousarray(adj if len(adj) else np.zeros(1, np.int32), dtype=np.int32)
+    f = lib().oracle_max_matching
+    f.restype = ctypes.c_int64
+    return int(f(_i32(nL), _i32(nR), _p(ptr), _p(adj)))
+
+
+def tile_graph(A, P: Plan, t: int):
+    """Bipartite graph of tile t: left = the row block's rows (local ids), right = the tile's Cols
+    positions, one edge per nonzero of the tile (input marshalling for max_matching)."""
+    p, q = P.tile_pq(t)
+    r0, r1 = int(P.rb[p]), int(P.rb[p + 1])
+    c0, c1 = int(P.cb[q]), int(P.cb[q + 1])
+    ptr = [0]
+    adj = []
+    for i in range(r0, r1):
+        s, e = int(A.rowptr[i]), int(A.rowptr[i + 1])
+        cols = A.col[s:e]
+        loc = P.colidx_local[s:e]
+        sel = (cols >= c0) & (cols < c1)
+        adj.extend(loc[sel].tolist())
+        ptr.append(len(adj))
+    return r1 - r0, int(P.tile_ncols[t]), np.array(ptr, np.int64), np.array(adj, np.int32)
+
+
 def scaled_error(C, C64, S) -> float:
     """max over elements of |C - C64| / S, where S = 0 requires C == 0 (returns inf otherwise)."""
     C = np.asarray(C, dtype=np.float64)

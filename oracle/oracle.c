@@ -19,7 +19,9 @@
  *   - the pack of B rows named by Cols (Sec. 5.1 stage 3) -- a plain row copy;
  *   - C = A B (Sec. 2.1) summed in FP64, both directly from B and through the packed rows;
  *   - the backward pieces dB = A^T dC and dA_ij = <dC_i,:, B_j,:> on A's pattern, and the
- *     CSR transpose with rows of A^T in ascending order of A's row index.
+ *     CSR transpose with rows of A^T in ascending order of A's row index;
+ *   - the maximum matching of a tile's row-column graph, whose size is the minimum vertex cover
+ *     mu of the joint row-column strategy (Sec. 5.3, Eq. 7-8; Koenig's theorem).
  *
  * Every loop is the definition written out: no blocking, fusion or reordering.  Floating-point
  * sums are taken in CSR order in FP64.  Build with -ffp-contract=off so every product and sum is
@@ -267,4 +269,54 @@ void oracle_transpose(int64_t M, int64_t K, const int64_t* rowptr, const int32_t
       perm[pos] = e;
     }
   free(fill);
+}
+
+/* Size of a maximum matching of the bipartite graph with left vertices 0..nL-1 (a tile's rows),
+ * right vertices 0..nR-1 (its columns) and edges adj[ptr[u] .. ptr[u+1]) of left vertex u (its
+ * nonzeros).  By Koenig's theorem this is the size mu of a minimum vertex cover, the optimum of
+ * Eq. 4-6 with uniform costs (Sec. 5.3.1 reduction, Sec. 5.4 uniform case).  Kuhn's method: for
+ * every left vertex, search an augmenting path depth first (explicit stack); levels remember the
+ * right vertex they were reached through so the path can be flipped. */
+int64_t oracle_max_matching(int32_t nL, int32_t nR, const int64_t* ptr, const int32_t* adj) {
+  int32_t* matchR = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nR > 0 ? nR : 1));
+  int64_t* seen = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nR > 0 ? nR : 1));
+  int32_t* su = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nL > 0 ? nL : 1));
+  int64_t* sk = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nL > 0 ? nL : 1));
+  int32_t* sv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nL > 0 ? nL : 1));
+  for (int32_t v = 0; v < nR; ++v) {
+    matchR[v] = -1;
+    seen[v] = -1;
+  }
+  int64_t size = 0;
+  for (int32_t root = 0; root < nL; ++root) {
+    int32_t d = 0;
+    su[0] = root;
+    sk[0] = ptr[root];
+    while (d >= 0) {
+      const int32_t u = su[d];
+      if (sk[d] == ptr[u + 1]) {
+        --d;
+        continue;
+      }
+      const int32_t v = adj[sk[d]++];
+      if (seen[v] == root) continue;
+      seen[v] = root;
+      if (matchR[v] < 0) {
+        matchR[v] = u;
+        for (int32_t l = d - 1; l >= 0; --l) matchR[sv[l]] = su[l];
+        ++size;
+        break;
+      }
+      sv[d] = v;
+      ++d;
+      su[d] = matchR[v];
+      sk[d] = ptr[su[d]];
+    }
+  }
+  free(matchR);
+  free(seen);
+  free(su);
+  free(sk);
+  free(sv);
+  return size;
 }

@@ -282,18 +282,23 @@ template <int VEC, int NCH, typename TB>
 struct Occupancy {
   // Registers per lane held by one gathered row fragment.
   static constexpr int REG = VEC * NCH * (int)(sizeof(typename AccOf<TB>::T) / 4);
-#ifdef SHIRO_SPMM_U
-  static constexpr int U = REG >= 16 ? 2 : SHIRO_SPMM_U;
-#else
-  static constexpr int U = REG >= 16 ? 2 : 4;
+#ifndef SHIRO_SPMM_U
+#define SHIRO_SPMM_U 4
 #endif
+#ifndef SHIRO_SPMM_U8
+#define SHIRO_SPMM_U8 2
+#endif
+  static constexpr int U = REG >= 16 ? 2 : (REG >= 8 ? SHIRO_SPMM_U8 : SHIRO_SPMM_U);
   // 64 registers for 4-register fragments (32 warps per SM): measured faster than 80 registers
   // without spills (24 warps), though ptxas spills a few bytes of the long-row epilogue.
-#ifdef SHIRO_SPMM_MIN_BLOCKS
-  static constexpr int MIN_BLOCKS = REG <= 4 ? SHIRO_SPMM_MIN_BLOCKS : 2;
-#else
-  static constexpr int MIN_BLOCKS = REG <= 4 ? 4 : 2;
+#ifndef SHIRO_SPMM_MIN_BLOCKS
+#define SHIRO_SPMM_MIN_BLOCKS 4
 #endif
+#ifndef SHIRO_SPMM_MIN_BLOCKS8
+#define SHIRO_SPMM_MIN_BLOCKS8 4
+#endif
+  static constexpr int MIN_BLOCKS =
+      REG <= 4 ? SHIRO_SPMM_MIN_BLOCKS : (REG <= 8 ? SHIRO_SPMM_MIN_BLOCKS8 : 2);
 };
 
 // Blocks [0, chunk_blocks) run the chunks of long rows, the others the row groups (the two

@@ -67,6 +67,9 @@ SIGNATURES = [
     ("shiro_plan_query", ctypes.c_int, [_vp, _P(shiro_plan_info)]),
     ("shiro_plan_tile_stats", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_volumes", ctypes.c_int, [_vp, _i32, ctypes.c_int, _vp, _vp, _vp]),
+    ("shiro_plan_joint", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("shiro_joint_split_sizes", ctypes.c_int, [_vp, _vp, _P(_i64), _P(_i64), _P(_i64)]),
+    ("shiro_joint_split", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_export", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_export_transpose", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_update_values", ctypes.c_int, [_vp, _vp, _vp]),
@@ -257,6 +260,14 @@ class Plan:
         shiro_plan_volumes(self.handle, int(N), dtype_code(dtype), _ptr(vb), _ptr(vc), _ptr(vr))
         return vb, vc, vr
 
+    def joint(self, stream=None):
+        """Per-tile minimum vertex cover (joint row-column strategy) and the side of every nonzero."""
+        T, n = self.info.n_tiles, self.info.nnz
+        mu, cr, cc = (torch.zeros(T, dtype=torch.int64) for _ in range(3))
+        side = torch.zeros(max(n, 1), dtype=torch.uint8)
+        shiro_plan_joint(self.handle, _ptr(mu), _ptr(cr), _ptr(cc), _ptr(side), _stream(stream))
+        return {"mu": mu, "cover_rows": cr, "cover_cols": cc, "row_based": side[:n]}
+
     def export(self, stream=None):
         i = self.info
         d = self.device
@@ -367,3 +378,56 @@ def spmm_backward(plan: Plan, planT: Plan, dC, Bpack, B=None, want_dB=True, want
                         _ptr(B), ldb, N, dtype_code(dC.dtype), _ptr(dCpack), N, _ptr(dB),
                         N, _ptr(dA), _ptr(scratch), sb, _stream(stream))
     return dB, dA
+
+
+class JointSpMM:
+    """C = A B by the joint row-column strategy (Sec. 5.2-5.3): A's tiles are split by a minimum
+    vertex cover into column-based nonzeros (packed B rows, plan_col) and row-based ones (partial
+    C rows computed where B lives, plan_rs, then added to C in tile order by plan_agg).  All the
+    arithmetic runs in the library; this class only allocates and sequences the calls."""
+
+    def __init__(self, plan: Plan, P_r, P_c, flags=0, row_bounds=None, col_bounds=None,
+                 opts=None):
+        self.base = plan
+        self.cover = plan.joint()
+        side = self.cover["row_based"].contiguous()
+        info = plan.info
+        dev = plan.device
+        cn, R, rn = _i64(0), _i64(0), _i64(0)
+        shiro_joint_split_sizes(plan.handle, _ptr(side), ctypes.byref(cn), ctypes.byref(R),
+                                ctypes.byref(rn))
+        self.split_rows = R.value
+        vdt = plan.vdt
+        M, K = info.M, info.K
+        z = lambda n, dt: torch.empty(max(int(n), 1), dtype=dt, device=dev)
+        self.col = (z(M + 1, torch.int64), z(cn.value, torch.int32), z(cn.value, vdt))
+        self.rs = (z(R.value + 1, torch.int64), z(rn.value, torch.int32), z(rn.value, vdt))
+        self.agg = (z(M + 1, torch.int64), z(R.value, torch.int32), z(R.value, vdt))
+        shiro_joint_split(plan.handle, _ptr(side), *[_ptr(t) for t in self.col],
+                          *[_ptr(t) for t in self.rs], *[_ptr(t) for t in self.agg],
+                          _stream(None))
+        col = (self.col[0], self.col[1][: cn.value], self.col[2][: cn.value])
+        self.plan_col = Plan.create(*col, M, K, P_r, P_c, row_bounds=row_bounds,
+                                    col_bounds=col_bounds, flags=flags, opts=opts)
+        self.plan_rs = self.plan_agg = None
+        if R.value > 0:
+            rs = (self.rs[0][: R.value + 1], self.rs[1][: rn.value], self.rs[2][: rn.value])
+            agg = (self.agg[0], self.agg[1][: R.value], self.agg[2][: R.value])
+            self.plan_rs = Plan.create(*rs, R.value, K, 1, 1, flags=SHIRO_PLAN_LOCAL_DIAG, opts=opts)
+            self.plan_agg = Plan.create(*agg, M, R.value, 1, 1, flags=SHIRO_PLAN_LOCAL_DIAG,
+                                        opts=opts)
+
+    def volumes(self):
+        """(rows of B sent, partial C rows sent): the two parts of mu (Eq. 9)."""
+        return self.plan_col.info.packed_rows, self.split_rows
+
+    def spmm(self, B, out=None, stream=None):
+        N = B.shape[1]
+        Bp = self.plan_col.pack(B, stream=stream)
+        C = self.plan_col.spmm(Bp, B=B, out=out, stream=stream)
+        if self.plan_rs is not None:
+            none = torch.empty((0, N), dtype=B.dtype, device=B.device)
+            part = self.plan_rs.spmm(none, B=B, stream=stream)
+            self.plan_agg.spmm(torch.empty((0, N), dtype=part.dtype, device=B.device), B=part,
+                               out=C, accumulate=True, stream=stream)
+        return C

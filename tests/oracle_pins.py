@@ -9,7 +9,9 @@ paper, never from the oracle's own code paths:
 * Python ``set`` brute force for Cols/Rows of every tile (Tab. 1, Eq. 2, Eq. 3) and the invariants
   Cols_t[colidx_local[e]] == col[e], sum_q |Cols(A^(p,q))| == |Cols(A^(p,:))|, V_block >= V_col;
 * |Cols(A^T tile (q,p))| == |Rows(A tile (p,q))|;
-* the worked example of Fig. 1 / Sec. 5.2, rebuilt from its captions (tests/golden).
+* the worked example of Fig. 1 / Sec. 5.2, rebuilt from its captions (tests/golden);
+* brute-force minimum vertex covers (the 0-1 program of Eq. 4-6 by enumeration) for the matching
+  size (Koenig's theorem), and a full row + full column pattern whose cover is 2.
 
 The same checks run against deliberately broken builds of the oracle (test_oracle_mutants.py), so a
 plausible mistake in it -- a dropped term, a wrong index or sign, a transposed operand, an
@@ -264,7 +266,51 @@ def check_er_band():
     assert np.all(np.abs(P.tile_ncols - mean) < 80)
 
 
-ALL_CHECKS = [check_spmm_dense, check_spmm_exact_structures, check_plan_bruteforce,
+def brute_min_cover(nL, nR, edges):
+    """Smallest set of rows and columns covering every edge (Eq. 4-6), by enumeration."""
+    verts = [("r", i) for i in range(nL)] + [("c", j) for j in range(nR)]
+    for k in range(len(verts) + 1):
+        for sel in itertools.combinations(verts, k):
+            ss = set(sel)
+            if all(("r", i) in ss or ("c", j) in ss for i, j in edges):
+                return k
+    return len(verts)
+
+
+def check_matching_is_min_cover():
+    for seed in range(40):
+        u = synth.uniform_f64(seed, synth.STREAM_PERM, 0, 3)
+        nL, nR = 1 + int(u[0] * 6), 1 + int(u[1] * 6)
+        dens = 0.15 + 0.6 * u[2]
+        m = synth.uniform_f64(seed, synth.STREAM_ER, 0, nL * nR).reshape(nL, nR) < dens
+        edges = [(i, j) for i in range(nL) for j in range(nR) if m[i, j]]
+        ptr = np.zeros(nL + 1, np.int64)
+        adj = []
+        for i in range(nL):
+            adj += [j for j in range(nR) if m[i, j]]
+            ptr[i + 1] = len(adj)
+        mu = oracle.max_matching(nL, nR, ptr, np.array(adj, np.int32))
+        assert mu == brute_min_cover(nL, nR, edges), "matching size != minimum vertex cover"
+    # Cross pattern (a full row and a full column, Sec. 5.4 pattern with hubs on both sides).
+    n = 9
+    adj = list(range(n)) + [0] * (n - 1)
+    ptr = np.array([0, n] + [n + i for i in range(1, n)], np.int64)
+    assert oracle.max_matching(n, n, ptr, np.array(adj, np.int32)) == 2
+
+
+def check_fig1_joint_cover():
+    nz, expect, meta = read_golden("fig1_offdiag_tile.txt")
+    M, K = meta["shape"]
+    Pr, Pc = meta["partition"]
+    D = np.zeros((M, K), dtype=np.float32)
+    for _, i, j in nz:
+        D[i, j] = 1.0
+    A = synth.from_dense(D)
+    P = oracle.plan(A, Pr, Pc)
+    assert oracle.max_matching(*oracle.tile_graph(A, P, 1)) == expect["min_cover"][0]
+
+
+ALL_CHECKS = [check_matching_is_min_cover, check_fig1_joint_cover, check_spmm_dense, check_spmm_exact_structures, check_plan_bruteforce,
               check_uniform_bounds, check_plan_diag_only, check_pack_and_packed_spmm,
               check_transpose_and_rows, check_backward_dense, check_abs_scale, check_fig1_golden,
               check_er_band]

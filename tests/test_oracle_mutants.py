@@ -22,6 +22,7 @@ MUTANTS = {
     "bounds_floor": ("int64_t b = (n + P - 1) / P;", "int64_t b = n / P > 0 ? n / P : 1;"),
     "rows_count_per_nnz": ("rows_t += row_hit;", "rows_t += row_hit ? (rowptr[i + 1] - rowptr[i]) : 0;"),
     "abs_scale_signed": ("const double a = fabs(val[e]);", "const double a = val[e];"),
+    "matching_no_flip": ("for (int32_t l = d - 1; l >= 0; --l) matchR[sv[l]] = su[l];", "(void)sv;"),
 }
 
 

@@ -248,6 +248,21 @@ def max_matching(nL: int, nR: int, ptr, adj) -> int:
     return int(f(_i32(nL), _i32(nR), _p(ptr), _p(adj)))
 
 
+def min_weight_cover(nL: int, nR: int, ptr, adj, w_row, w_col):
+    """Minimum weighted vertex cover of a bipartite graph by the minimum cut of Sec. 5.3.3.
+    Returns (max flow, cover_row bool[nL], cover_col bool[nR])."""
+    ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+    adj = np.ascontiguousarray(adj if len(adj) else np.zeros(1, np.int32), dtype=np.int32)
+    wr = np.ascontiguousarray(w_row if nL else np.zeros(1), dtype=np.int64)
+    wc = np.ascontiguousarray(w_col if nR else np.zeros(1), dtype=np.int64)
+    cr = np.zeros(max(nL, 1), np.uint8)
+    cc = np.zeros(max(nR, 1), np.uint8)
+    f = lib().oracle_min_weight_cover
+    f.restype = ctypes.c_int64
+    flow = int(f(_i32(nL), _i32(nR), _p(ptr), _p(adj), _p(wr), _p(wc), _p(cr), _p(cc)))
+    return flow, cr[:nL].astype(bool), cc[:nR].astype(bool)
+
+
 def tile_graph(A, P: Plan, t: int):
     """Bipartite graph of tile t: left = the row block's rows (local ids), right = the tile's Cols
     positions, one edge per nonzero of the tile (input marshalling for max_matching)."""

@@ -21,7 +21,9 @@
  *   - the backward pieces dB = A^T dC and dA_ij = <dC_i,:, B_j,:> on A's pattern, and the
  *     CSR transpose with rows of A^T in ascending order of A's row index;
  *   - the maximum matching of a tile's row-column graph, whose size is the minimum vertex cover
- *     mu of the joint row-column strategy (Sec. 5.3, Eq. 7-8; Koenig's theorem).
+ *     mu of the joint row-column strategy (Sec. 5.3, Eq. 7-8; Koenig's theorem);
+ *   - the minimum weighted vertex cover of that graph through the flow network and minimum cut
+ *     of Sec. 5.3.3.
  *
  * Every loop is the definition written out: no blocking, fusion or reordering.  Floating-point
  * sums are taken in CSR order in FP64.  Build with -ffp-contract=off so every product and sum is
@@ -319,4 +321,80 @@ int64_t oracle_max_matching(int32_t nL, int32_t nR, const int64_t* ptr, const in
   free(sk);
   free(sv);
   return size;
+}
+
+/* Minimum weighted vertex cover of the bipartite row-column graph of a tile (Sec. 5.3.2: Eq. 4-6
+ * with a cost per vertex, w_row[u] for sending partial row c_u, w_col[v] for sending row b_v).
+ * Sec. 5.3.3 turns it into a minimum s-t cut: the source feeds row u with capacity w_row[u],
+ * every nonzero (u, v) links row u to column v with unbounded capacity, column v feeds the sink
+ * with capacity w_col[v].  The maximum flow is found here by shortest augmenting paths
+ * (Edmonds-Karp; the paper's Dinic reaches the same flow value), and the cut is read off the set Z
+ * of vertices reachable from the source in the residual network: a row outside Z or a column
+ * inside Z is selected.  Z is the same for every maximum flow (it is the smallest source side of
+ * a minimum cut), so the selection is unique.  Rows without edges are never selected.
+ * cover_row (nL bytes) and cover_col (nR bytes) receive the selection; returns the maximum
+ * flow, which equals the selection's total cost (max-flow min-cut).  Costs must be >= 0 with a
+ * sum below 2^62. */
+int64_t oracle_min_weight_cover(int32_t nL, int32_t nR, const int64_t* ptr, const int32_t* adj,
+                                const int64_t* w_row, const int64_t* w_col, uint8_t* cover_row,
+                                uint8_t* cover_col) {
+  const int64_t UNBOUNDED = (int64_t)1 << 62;
+  const int64_t E = ptr[nL];
+  const int32_t n = nL + nR + 2, s = 0, t = nL + nR + 1;
+  const int64_t m = 2 * ((int64_t)nL + E + nR); /* every arc and its residual twin */
+  int32_t* to = (int32_t*)malloc(sizeof(int32_t) * (size_t)m);
+  int64_t* cap = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+  int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+  int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t* via = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  for (int32_t x = 0; x < n; ++x) head[x] = -1;
+  int64_t a = 0;
+  /* arc 2k goes forward with the capacity, arc 2k+1 is its twin with none: twin(e) = e ^ 1 */
+#define ORACLE_ARC(x, y, c)                                   \
+  do {                                                        \
+    to[a] = (y); cap[a] = (c); next[a] = head[x]; head[x] = a; ++a; \
+    to[a] = (x); cap[a] = 0; next[a] = head[y]; head[y] = a; ++a;   \
+  } while (0)
+  for (int32_t u = 0; u < nL; ++u) ORACLE_ARC(s, 1 + u, w_row[u]);
+  for (int32_t u = 0; u < nL; ++u)
+    for (int64_t k = ptr[u]; k < ptr[u + 1]; ++k) ORACLE_ARC(1 + u, 1 + nL + adj[k], UNBOUNDED);
+  for (int32_t v = 0; v < nR; ++v) ORACLE_ARC(1 + nL + v, t, w_col[v]);
+#undef ORACLE_ARC
+  int64_t flow = 0;
+  for (;;) {
+    /* breadth-first search for a shortest path with residual capacity */
+    for (int32_t x = 0; x < n; ++x) via[x] = -2;
+    via[s] = -1;
+    int32_t qh = 0, qt = 0;
+    queue[qt++] = s;
+    while (qh < qt && via[t] == -2) {
+      const int32_t x = queue[qh++];
+      for (int64_t e = head[x]; e >= 0; e = next[e])
+        if (cap[e] > 0 && via[to[e]] == -2) {
+          via[to[e]] = e;
+          queue[qt++] = to[e];
+        }
+    }
+    if (via[t] == -2) break;
+    int64_t b = UNBOUNDED;
+    for (int32_t x = t; x != s; x = to[via[x] ^ 1])
+      if (cap[via[x]] < b) b = cap[via[x]];
+    for (int32_t x = t; x != s; x = to[via[x] ^ 1]) {
+      cap[via[x]] -= b;
+      cap[via[x] ^ 1] += b;
+    }
+    flow += b;
+  }
+  /* Z: reachable from the source through arcs with residual capacity (via[] != -2 after the last
+   * search, which ran to exhaustion because the sink was not reached) */
+  for (int32_t u = 0; u < nL; ++u) cover_row[u] = (uint8_t)(via[1 + u] == -2 && ptr[u + 1] > ptr[u]);
+  for (int32_t v = 0; v < nR; ++v) cover_col[v] = (uint8_t)(via[1 + nL + v] != -2);
+  free(to);
+  free(cap);
+  free(next);
+  free(head);
+  free(via);
+  free(queue);
+  return flow;
 }

@@ -310,7 +310,99 @@ def check_fig1_joint_cover():
     assert oracle.max_matching(*oracle.tile_graph(A, P, 1)) == expect["min_cover"][0]
 
 
-ALL_CHECKS = [check_matching_is_min_cover, check_fig1_joint_cover, check_spmm_dense, check_spmm_exact_structures, check_plan_bruteforce,
+def _tiny_graph(seed, max_side=7):
+    u = synth.uniform_f64(seed, synth.STREAM_PERM, 0, 3)
+    nL, nR = 1 + int(u[0] * max_side), 1 + int(u[1] * max_side)
+    dens = 0.15 + 0.6 * u[2]
+    m = synth.uniform_f64(seed, synth.STREAM_ER, 0, nL * nR).reshape(nL, nR) < dens
+    ptr = np.zeros(nL + 1, np.int64)
+    adj = []
+    for i in range(nL):
+        adj += [j for j in range(nR) if m[i, j]]
+        ptr[i + 1] = len(adj)
+    return nL, nR, ptr, np.array(adj, np.int32), m
+
+
+def brute_weighted_covers(nL, nR, m, w_row, w_col):
+    """All covers of minimum cost (Eq. 4-6 with per-vertex costs), by enumerating the selected
+    rows; the columns are then forced: every neighbour of an unselected row.  Returns the minimum
+    cost and the list of (row set, column set) reaching it (costs > 0, so no extra vertex is ever
+    free)."""
+    best, covers = None, []
+    for mask in range(1 << nL):
+        rows = {i for i in range(nL) if mask >> i & 1}
+        cols = {j for i in range(nL) if i not in rows for j in range(nR) if m[i, j]}
+        c = sum(int(w_row[i]) for i in rows) + sum(int(w_col[j]) for j in cols)
+        if best is None or c < best:
+            best, covers = c, [(rows, cols)]
+        elif c == best:
+            covers.append((rows, cols))
+    return best, covers
+
+
+def check_weighted_cover_bruteforce():
+    """Min cut of Sec. 5.3.3 = minimum weighted vertex cover (Eq. 4-6), and the selection read off
+    the residual reachability is the minimum cover whose column set lies inside every other's."""
+    for seed in range(60):
+        nL, nR, ptr, adj, m = _tiny_graph(seed)
+        w = synth.uniform_f64(seed, synth.STREAM_VAL, 0, nL + nR)
+        w_row = 1 + (w[:nL] * 9).astype(np.int64)
+        w_col = 1 + (w[nL:] * 9).astype(np.int64)
+        flow, cr, cc = oracle.min_weight_cover(nL, nR, ptr, adj, w_row, w_col)
+        best, covers = brute_weighted_covers(nL, nR, m, w_row, w_col)
+        assert flow == best, f"max flow {flow} != minimum cover cost {best}"
+        assert int(w_row[cr].sum() + w_col[cc].sum()) == flow, "cut cost != max flow"
+        assert all(cr[i] or cc[j] for i in range(nL) for j in range(nR) if m[i, j]), "edge uncovered"
+        inter = set(range(nR))
+        for _, cols in covers:
+            inter &= cols
+        assert set(np.flatnonzero(cc).tolist()) == inter, "cover is not the source-minimal cut"
+        assert not np.any(cr & (np.diff(ptr) == 0)), "isolated row selected"
+
+
+def check_weighted_cover_special_cases():
+    """Uniform costs reduce to Koenig (cost = c * maximum matching); one side far dearer than
+    the other selects every non-isolated vertex of the cheap side; zero costs are free."""
+    for seed in range(30):
+        nL, nR, ptr, adj, m = _tiny_graph(100 + seed)
+        mu = oracle.max_matching(nL, nR, ptr, adj)
+        for c in (1, 7):
+            flow, _, _ = oracle.min_weight_cover(nL, nR, ptr, adj, np.full(nL, c), np.full(nR, c))
+            assert flow == c * mu, "uniform costs must give c * mu"
+        used_cols = m.any(axis=0)
+        used_rows = m.any(axis=1)
+        big = 100 * (nL + nR)
+        flow, cr, cc = oracle.min_weight_cover(nL, nR, ptr, adj, np.full(nL, big), np.ones(nR))
+        assert flow == int(used_cols.sum()) and not cr.any() and np.array_equal(cc, used_cols)
+        flow, cr, cc = oracle.min_weight_cover(nL, nR, ptr, adj, np.ones(nL), np.full(nR, big))
+        assert flow == int(used_rows.sum()) and not cc.any() and np.array_equal(cr, used_rows)
+        flow, cr, cc = oracle.min_weight_cover(nL, nR, ptr, adj, np.ones(nL), np.zeros(nR))
+        assert flow == 0 and np.array_equal(cc, used_cols) and not cr.any()
+    # A star: one row on five columns costs its row when rows are cheaper than five columns.
+    ptr = np.array([0, 5], np.int64)
+    adj = np.arange(5, dtype=np.int32)
+    assert oracle.min_weight_cover(1, 5, ptr, adj, [4], np.ones(5))[0] == 4
+    assert oracle.min_weight_cover(1, 5, ptr, adj, [6], np.ones(5))[0] == 5
+
+
+def check_fig1_weighted_cover():
+    """The off-diagonal tile of the Fig. 1 example: unit costs give the joint optimum of the
+    golden file; its cover is a valid one of that size."""
+    nz, expect, meta = read_golden("fig1_offdiag_tile.txt")
+    M, K = meta["shape"]
+    Pr, Pc = meta["partition"]
+    D = np.zeros((M, K), dtype=np.float32)
+    for _, i, j in nz:
+        D[i, j] = 1.0
+    A = synth.from_dense(D)
+    P = oracle.plan(A, Pr, Pc)
+    nL, nR, ptr, adj = oracle.tile_graph(A, P, 1)
+    flow, cr, cc = oracle.min_weight_cover(nL, nR, ptr, adj, np.ones(nL), np.ones(nR))
+    assert flow == expect["min_cover"][0] == int(cr.sum() + cc.sum())
+
+
+ALL_CHECKS = [check_weighted_cover_bruteforce, check_weighted_cover_special_cases,
+              check_fig1_weighted_cover, check_matching_is_min_cover, check_fig1_joint_cover, check_spmm_dense, check_spmm_exact_structures, check_plan_bruteforce,
               check_uniform_bounds, check_plan_diag_only, check_pack_and_packed_spmm,
               check_transpose_and_rows, check_backward_dense, check_abs_scale, check_fig1_golden,
               check_er_band]

@@ -22,6 +22,9 @@ MUTANTS = {
     "bounds_floor": ("int64_t b = (n + P - 1) / P;", "int64_t b = n / P > 0 ? n / P : 1;"),
     "rows_count_per_nnz": ("rows_t += row_hit;", "rows_t += row_hit ? (rowptr[i + 1] - rowptr[i]) : 0;"),
     "abs_scale_signed": ("const double a = fabs(val[e]);", "const double a = val[e];"),
+    "cut_read_flipped": ("cover_col[v] = (uint8_t)(via[1 + nL + v] != -2);", "cover_col[v] = (uint8_t)(via[1 + nL + v] == -2);"),
+    "no_residual_twin": ("cap[via[x] ^ 1] += b;", "(void)0;"),
+    "source_capacity_wrong": ("ORACLE_ARC(s, 1 + u, w_row[u]);", "ORACLE_ARC(s, 1 + u, w_row[u] + (u == 0));"),
     "matching_no_flip": ("for (int32_t l = d - 1; l >= 0; --l) matchR[sv[l]] = su[l];", "(void)sv;"),
 }
 

@@ -168,6 +168,31 @@ shiro_status shiro_plan_volumes(shiro_plan_t plan, int32_t N, shiro_dtype dt, in
 shiro_status shiro_plan_joint(shiro_plan_t plan, int64_t* tile_mu, int64_t* tile_cover_rows,
                               int64_t* tile_cover_cols, uint8_t* nnz_row_based, void* stream);
 
+/* Weighted joint strategy (Sec. 5.3.2-5.3.3): per tile, the minimum weighted vertex cover of the
+ * row-column graph, with cost w_row[i] for sending the partial row c_i and w_col[j] for sending
+ * row b_j (e.g. N * sizeof(C accumulator) and N * sizeof(B element) when B and the partial rows
+ * differ in type).  Solved as the minimum s-t cut of the network source -> row (w_row) -> column
+ * (unbounded, one arc per nonzero) -> sink (w_col) by Dinic's algorithm; the selection is read
+ * off the vertices reachable from the source in the final residual network, which is the same for
+ * every maximum flow, so the cover is unique (with all costs 1 it equals shiro_plan_joint's).
+ * w_row (host, M entries, indexed by global row) or NULL for a uniform w_row_all; w_col (host, K
+ * entries, indexed by global column) or NULL for w_col_all.  Costs must be >= 0 and each side's
+ * total at most 2^60, else SHIRO_ERR_INVALID_ARG.  Outputs as shiro_plan_joint, with tile_cost
+ * the cover's total cost (= the maximum flow).  Offline host work; synchronises `stream`. */
+shiro_status shiro_plan_joint_weighted(shiro_plan_t plan, const int64_t* w_row,
+                                       const int64_t* w_col, int64_t w_row_all, int64_t w_col_all,
+                                       int64_t* tile_cost, int64_t* tile_cover_rows,
+                                       int64_t* tile_cover_cols, uint8_t* nnz_row_based,
+                                       void* stream);
+
+/* Row-based strategy (Eq. 3) as a side assignment for shiro_joint_split: every nonzero of a
+ * communicated tile is row-based (nnz_row_based = 1; 0 on the local diagonal tiles of a
+ * LOCAL_DIAG plan), so the owners of B send one partial C row per row of Rows(A^(p,q)).
+ * tile_rows (host, n_tiles) receives |Rows| of every communicated tile (0 for local ones).
+ * Synchronises `stream`. */
+shiro_status shiro_plan_row_based(shiro_plan_t plan, int64_t* tile_rows, uint8_t* nnz_row_based,
+                                  void* stream);
+
 /* Split of A by a joint cover (nnz_row_based from shiro_plan_joint, host, nnz bytes) into the
  * three CSR matrices whose SpMMs compute C = A B the joint way (Sec. 5.1 stages 3 and 5):
  *   A_col (M x K): the column-based nonzeros, to be planned on the same grid -- its tiles' Cols are

@@ -133,76 +133,218 @@ void koenig_cover(const Bipartite& g, const std::vector<int32_t>& pairL,
   for (int32_t v = 0; v < g.nR; ++v) coverR[v] = zR[v];
 }
 
+
+// Minimum weighted vertex cover through the minimum s-t cut of Sec. 5.3.3: source -> row u with
+// capacity w_row[u], row -> column with unbounded capacity for every edge, column v -> sink with
+// capacity w_col[v].  Dinic's algorithm (BFS level graph, blocking flow by an iterative DFS that
+// retreats to the first saturated arc after each augmentation).  The cover is read off the set Z
+// reachable from the source in the final residual network (rows outside Z, columns inside Z):
+// that set is the same for every maximum flow, so the selection does not depend on the search
+// order.  Returns the maximum flow (= the cover's cost).
+struct FlowNet {
+  int32_t n = 0;
+  std::vector<int64_t> first;  // arcs of node x: [first[x], first[x+1])
+  std::vector<int32_t> to;
+  std::vector<int64_t> twin;
+  std::vector<int64_t> cap;
+};
+
+int64_t dinic_cover(const Bipartite& g, const std::vector<int64_t>& w_row,
+                    const std::vector<int64_t>& w_col, std::vector<char>& coverL,
+                    std::vector<char>& coverR) {
+  const int64_t UNBOUNDED = (int64_t)1 << 62;
+  const int32_t nL = g.nL, nR = g.nR, s = 0, t = nL + nR + 1;
+  FlowNet f;
+  f.n = nL + nR + 2;
+  // Arc counts per node: s has nL, row u has 1 + deg(u), column v has in-degree + 1, t has nR.
+  std::vector<int64_t> deg(f.n + 1, 0);
+  deg[s] = nL;
+  for (int32_t u = 0; u < nL; ++u) deg[1 + u] = 1 + (g.ptr[u + 1] - g.ptr[u]);
+  for (int32_t v = 0; v < nR; ++v) deg[1 + nL + v] = 1;
+  for (int64_t k = 0; k < g.ptr[nL]; ++k) deg[1 + nL + g.adj[k]] += 1;
+  deg[t] = nR;
+  f.first.assign(f.n + 1, 0);
+  for (int32_t x = 0; x < f.n; ++x) f.first[x + 1] = f.first[x] + deg[x];
+  const int64_t m = f.first[f.n];
+  f.to.resize(m);
+  f.twin.resize(m);
+  f.cap.resize(m);
+  std::vector<int64_t> fill(f.first.begin(), f.first.end() - 1);
+  auto arc = [&](int32_t x, int32_t y, int64_t c) {
+    const int64_t a = fill[x]++, b = fill[y]++;
+    f.to[a] = y; f.cap[a] = c; f.twin[a] = b;
+    f.to[b] = x; f.cap[b] = 0; f.twin[b] = a;
+  };
+  for (int32_t u = 0; u < nL; ++u) arc(s, 1 + u, w_row[u]);
+  for (int32_t u = 0; u < nL; ++u)
+    for (int64_t k = g.ptr[u]; k < g.ptr[u + 1]; ++k) arc(1 + u, 1 + nL + g.adj[k], UNBOUNDED);
+  for (int32_t v = 0; v < nR; ++v) arc(1 + nL + v, t, w_col[v]);
+
+  std::vector<int32_t> level(f.n), queue(f.n);
+  std::vector<int64_t> it(f.n), path;
+  path.reserve(64);
+  auto bfs = [&]() {
+    std::fill(level.begin(), level.end(), -1);
+    int32_t qh = 0, qt = 0;
+    level[s] = 0;
+    queue[qt++] = s;
+    while (qh < qt) {
+      const int32_t x = queue[qh++];
+      for (int64_t a = f.first[x]; a < f.first[x + 1]; ++a)
+        if (f.cap[a] > 0 && level[f.to[a]] < 0) {
+          level[f.to[a]] = level[x] + 1;
+          queue[qt++] = f.to[a];
+        }
+    }
+    return level[t] >= 0;
+  };
+  int64_t flow = 0;
+  while (bfs()) {
+    for (int32_t x = 0; x < f.n; ++x) it[x] = f.first[x];
+    path.clear();
+    int32_t x = s;
+    while (true) {
+      if (x == t) {
+        int64_t b = UNBOUNDED;
+        for (int64_t a : path) b = std::min(b, f.cap[a]);
+        size_t cut = path.size();
+        for (size_t k = 0; k < path.size(); ++k) {
+          f.cap[path[k]] -= b;
+          f.cap[f.twin[path[k]]] += b;
+          if (f.cap[path[k]] == 0 && cut == path.size()) cut = k;
+        }
+        flow += b;
+        // Retreat to the tail of the first saturated arc and continue the blocking flow there.
+        x = f.to[f.twin[path[cut]]];
+        path.resize(cut);
+        continue;
+      }
+      bool advanced = false;
+      for (; it[x] < f.first[x + 1]; ++it[x]) {
+        const int64_t a = it[x];
+        if (f.cap[a] > 0 && level[f.to[a]] == level[x] + 1) {
+          path.push_back(a);
+          x = f.to[a];
+          advanced = true;
+          break;
+        }
+      }
+      if (advanced) continue;
+      if (x == s) break;
+      level[x] = -1;  // dead end for the rest of this phase
+      const int64_t a = path.back();
+      path.pop_back();
+      x = f.to[f.twin[a]];
+      ++it[x];
+    }
+  }
+  // Z: reachable from the source through arcs with residual capacity.
+  std::vector<char> z(f.n, 0);
+  int32_t qh = 0, qt = 0;
+  z[s] = 1;
+  queue[qt++] = s;
+  while (qh < qt) {
+    const int32_t x = queue[qh++];
+    for (int64_t a = f.first[x]; a < f.first[x + 1]; ++a)
+      if (f.cap[a] > 0 && !z[f.to[a]]) {
+        z[f.to[a]] = 1;
+        queue[qt++] = f.to[a];
+      }
+  }
+  coverL.assign(nL, 0);
+  coverR.assign(nR, 0);
+  for (int32_t u = 0; u < nL; ++u) coverL[u] = (!z[1 + u] && g.ptr[u + 1] > g.ptr[u]) ? 1 : 0;
+  for (int32_t v = 0; v < nR; ++v) coverR[v] = z[1 + nL + v];
+  return flow;
+}
+
 }  // namespace
 
 }  // namespace shiro
 
 using namespace shiro;
 
-extern "C" shiro_status shiro_plan_joint(shiro_plan_t P, int64_t* tile_mu,
-                                         int64_t* tile_cover_rows, int64_t* tile_cover_cols,
-                                         uint8_t* nnz_row_based, void* stream) {
-  if (!P) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
-  cudaStream_t s = (cudaStream_t)stream;
+namespace {
+
+// Host view of the plan's tiles: the tile and the rank in its tile's Cols of every nonzero.
+struct TileIndex {
+  std::vector<int32_t> col, local, tile_of, cols_sorted;
+};
+
+shiro_status tile_index(const shiro_plan_s* P, TileIndex& X, cudaStream_t s) {
   const int64_t nnz = P->nnz;
-  std::vector<int32_t> col(nnz > 0 ? nnz : 1), local(nnz > 0 ? nnz : 1);
+  X.col.assign(nnz > 0 ? nnz : 1, 0);
+  X.local.assign(nnz > 0 ? nnz : 1, 0);
+  X.tile_of.assign(nnz > 0 ? nnz : 1, 0);
+  X.cols_sorted.assign(P->total_cols > 0 ? P->total_cols : 1, 0);
   if (nnz > 0)
-    SHIRO_CUDA(cudaMemcpyAsync(col.data(), P->col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
+    SHIRO_CUDA(cudaMemcpyAsync(X.col.data(), P->col, sizeof(int32_t) * nnz,
+                               cudaMemcpyDeviceToHost, s));
+  if (P->total_cols > 0)
+    SHIRO_CUDA(cudaMemcpyAsync(X.cols_sorted.data(), P->d_cols_sorted,
+                               sizeof(int32_t) * P->total_cols, cudaMemcpyDeviceToHost, s));
   SHIRO_CUDA(cudaStreamSynchronize(s));
   const bool diag = P->flags & SHIRO_PLAN_DIAG_ONLY;
-  const bool local_diag = P->flags & SHIRO_PLAN_LOCAL_DIAG;
-  const int32_t T = P->T, Pc = P->geo.Pc;
-  // Column block of every column and the rank of a column inside its tile's Cols.
-  auto col_block_h = [&](int64_t j) {
-    return (int32_t)(std::upper_bound(P->cb.begin(), P->cb.end(), j) - P->cb.begin() - 1);
-  };
-  std::vector<int32_t> cols_sorted(P->total_cols > 0 ? P->total_cols : 1);
-  if (P->total_cols > 0) {
-    SHIRO_CUDA(cudaMemcpyAsync(cols_sorted.data(), P->d_cols_sorted,
-                               sizeof(int32_t) * P->total_cols, cudaMemcpyDeviceToHost, s));
-    SHIRO_CUDA(cudaStreamSynchronize(s));
-  }
-  std::vector<int32_t> tile_of(nnz > 0 ? nnz : 1);
+  const int32_t Pc = P->geo.Pc;
   for (int32_t p = 0; p < P->geo.Pr; ++p)
     for (int64_t i = P->rb[p]; i < P->rb[p + 1]; ++i)
       for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e) {
-        const int32_t q = diag ? p : col_block_h(col[e]);
+        const int32_t q = diag ? p : (int32_t)(std::upper_bound(P->cb.begin(), P->cb.end(),
+                                                                (int64_t)X.col[e]) - P->cb.begin() - 1);
         const int32_t t = diag ? p : p * Pc + q;
-        tile_of[e] = t;
-        const int32_t* c0 = cols_sorted.data() + P->tile_cols_ptr[t];
-        const int32_t* c1 = cols_sorted.data() + P->tile_cols_ptr[t + 1];
-        local[e] = (int32_t)(std::lower_bound(c0, c1, col[e]) - c0);
+        X.tile_of[e] = t;
+        const int32_t* c0 = X.cols_sorted.data() + P->tile_cols_ptr[t];
+        const int32_t* c1 = X.cols_sorted.data() + P->tile_cols_ptr[t + 1];
+        X.local[e] = (int32_t)(std::lower_bound(c0, c1, X.col[e]) - c0);
       }
-  std::vector<int64_t> mu(T, 0), crows(T, 0), ccols(T, 0);
-  std::vector<uint8_t> side(nnz > 0 ? nnz : 1, 0);
+  return SHIRO_OK;
+}
+
+// The bipartite graph of tile t: left = the row block's rows (local ids), right = the tile's Cols
+// positions, one edge per nonzero.
+Bipartite tile_bipartite(const shiro_plan_s* P, const TileIndex& X, int32_t t) {
+  const bool diag = P->flags & SHIRO_PLAN_DIAG_ONLY;
+  const int32_t p = diag ? t : t / P->geo.Pc;
+  Bipartite g;
+  g.nL = (int32_t)(P->rb[p + 1] - P->rb[p]);
+  g.nR = (int32_t)P->tile_ncols[t];
+  g.ptr.assign(g.nL + 1, 0);
+  for (int32_t u = 0; u < g.nL; ++u) {
+    const int64_t i = P->rb[p] + u;
+    int64_t cnt = 0;
+    for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e) cnt += X.tile_of[e] == t;
+    g.ptr[u + 1] = g.ptr[u] + cnt;
+  }
+  g.adj.resize(g.ptr[g.nL]);
+  for (int32_t u = 0; u < g.nL; ++u) {
+    const int64_t i = P->rb[p] + u;
+    int64_t k = g.ptr[u];
+    for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e)
+      if (X.tile_of[e] == t) g.adj[k++] = X.local[e];
+  }
+  return g;
+}
+
+// Runs solve(t, g, coverL, coverR) -> cost on every communicated tile in parallel host threads
+// and gathers per-tile costs, cover sizes and the side of every nonzero (1 = row-based).
+template <class Solve>
+void solve_tiles(const shiro_plan_s* P, const TileIndex& X, Solve solve, int64_t* tile_cost,
+                 int64_t* tile_cover_rows, int64_t* tile_cover_cols, uint8_t* nnz_row_based) {
+  const int32_t T = P->T;
+  const bool diag = P->flags & SHIRO_PLAN_DIAG_ONLY;
+  const bool local_diag = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  std::vector<int64_t> cost(T, 0), crows(T, 0), ccols(T, 0);
+  std::vector<uint8_t> side(P->nnz > 0 ? P->nnz : 1, 0);
   std::atomic<int32_t> next{0};
   auto worker = [&]() {
     while (true) {
       const int32_t t = next.fetch_add(1);
       if (t >= T) break;
-      const int32_t p = diag ? t : t / Pc, q = diag ? t : t % Pc;
+      const int32_t p = diag ? t : t / P->geo.Pc, q = diag ? t : t % P->geo.Pc;
       if (local_diag && p == q) continue;  // local tile: nothing is communicated
-      Bipartite g;
-      g.nL = (int32_t)(P->rb[p + 1] - P->rb[p]);
-      g.nR = (int32_t)P->tile_ncols[t];
-      g.ptr.assign(g.nL + 1, 0);
-      for (int32_t u = 0; u < g.nL; ++u) {
-        const int64_t i = P->rb[p] + u;
-        int64_t cnt = 0;
-        for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e) cnt += tile_of[e] == t;
-        g.ptr[u + 1] = g.ptr[u] + cnt;
-      }
-      g.adj.resize(g.ptr[g.nL]);
-      for (int32_t u = 0; u < g.nL; ++u) {
-        const int64_t i = P->rb[p] + u;
-        int64_t k = g.ptr[u];
-        for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e)
-          if (tile_of[e] == t) g.adj[k++] = local[e];
-      }
-      std::vector<int32_t> pairL, pairR;
-      mu[t] = hopcroft_karp(g, pairL, pairR);
+      const Bipartite g = tile_bipartite(P, X, t);
       std::vector<char> coverL, coverR;
-      koenig_cover(g, pairL, pairR, coverL, coverR);
+      cost[t] = solve(t, g, coverL, coverR);
       int64_t nr = 0, nc = 0;
       for (char c : coverL) nr += c;
       for (char c : coverR) nc += c;
@@ -211,7 +353,7 @@ extern "C" shiro_status shiro_plan_joint(shiro_plan_t P, int64_t* tile_mu,
       for (int32_t u = 0; u < g.nL; ++u) {
         const int64_t i = P->rb[p] + u;
         for (int64_t e = P->h_rowptr[i]; e < P->h_rowptr[i + 1]; ++e)
-          if (tile_of[e] == t) side[e] = coverR[local[e]] ? 0 : 1;
+          if (X.tile_of[e] == t) side[e] = coverR[X.local[e]] ? 0 : 1;
       }
     }
   };
@@ -220,10 +362,89 @@ extern "C" shiro_status shiro_plan_joint(shiro_plan_t P, int64_t* tile_mu,
   for (unsigned k = 1; k < nt; ++k) pool.emplace_back(worker);
   worker();
   for (auto& th : pool) th.join();
-  if (tile_mu) memcpy(tile_mu, mu.data(), sizeof(int64_t) * T);
+  if (tile_cost) memcpy(tile_cost, cost.data(), sizeof(int64_t) * T);
   if (tile_cover_rows) memcpy(tile_cover_rows, crows.data(), sizeof(int64_t) * T);
   if (tile_cover_cols) memcpy(tile_cover_cols, ccols.data(), sizeof(int64_t) * T);
-  if (nnz_row_based && nnz > 0) memcpy(nnz_row_based, side.data(), (size_t)nnz);
+  if (nnz_row_based && P->nnz > 0) memcpy(nnz_row_based, side.data(), (size_t)P->nnz);
+}
+
+}  // namespace
+
+extern "C" shiro_status shiro_plan_joint(shiro_plan_t P, int64_t* tile_mu,
+                                         int64_t* tile_cover_rows, int64_t* tile_cover_cols,
+                                         uint8_t* nnz_row_based, void* stream) {
+  if (!P) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  TileIndex X;
+  SHIRO_TRY(tile_index(P, X, (cudaStream_t)stream));
+  auto solve = [](int32_t, const Bipartite& g, std::vector<char>& cl, std::vector<char>& cr) {
+    std::vector<int32_t> pairL, pairR;
+    const int64_t mu = hopcroft_karp(g, pairL, pairR);
+    koenig_cover(g, pairL, pairR, cl, cr);
+    return mu;
+  };
+  solve_tiles(P, X, solve, tile_mu, tile_cover_rows, tile_cover_cols, nnz_row_based);
+  return SHIRO_OK;
+}
+
+extern "C" shiro_status shiro_plan_joint_weighted(shiro_plan_t P, const int64_t* w_row,
+                                                  const int64_t* w_col, int64_t w_row_all,
+                                                  int64_t w_col_all, int64_t* tile_cost,
+                                                  int64_t* tile_cover_rows,
+                                                  int64_t* tile_cover_cols,
+                                                  uint8_t* nnz_row_based, void* stream) {
+  if (!P) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  // Costs must be >= 0 and every tile's total below 2^62 (the unbounded arc capacity).
+  const int64_t LIMIT = ((int64_t)1 << 62) / 4;
+  if (!w_row && (w_row_all < 0 || w_row_all > LIMIT / std::max<int64_t>(1, P->M)))
+    SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "row cost out of range");
+  if (!w_col && (w_col_all < 0 || w_col_all > LIMIT / std::max<int64_t>(1, P->K)))
+    SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "column cost out of range");
+  int64_t sum = 0;
+  if (w_row)
+    for (int64_t i = 0; i < P->M; ++i) {
+      if (w_row[i] < 0 || w_row[i] > LIMIT) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "row cost out of range");
+      sum += w_row[i];
+      if (sum > LIMIT) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "row costs sum too large");
+    }
+  sum = 0;
+  if (w_col)
+    for (int64_t j = 0; j < P->K; ++j) {
+      if (w_col[j] < 0 || w_col[j] > LIMIT) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "column cost out of range");
+      sum += w_col[j];
+      if (sum > LIMIT) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "column costs sum too large");
+    }
+  TileIndex X;
+  SHIRO_TRY(tile_index(P, X, (cudaStream_t)stream));
+  const bool diag = P->flags & SHIRO_PLAN_DIAG_ONLY;
+  auto solve = [&](int32_t t, const Bipartite& g, std::vector<char>& cl, std::vector<char>& cr) {
+    const int32_t p = diag ? t : t / P->geo.Pc;
+    std::vector<int64_t> wr(g.nL), wc(g.nR);
+    for (int32_t u = 0; u < g.nL; ++u) wr[u] = w_row ? w_row[P->rb[p] + u] : w_row_all;
+    const int32_t* cols = X.cols_sorted.data() + P->tile_cols_ptr[t];
+    for (int32_t v = 0; v < g.nR; ++v) wc[v] = w_col ? w_col[cols[v]] : w_col_all;
+    return dinic_cover(g, wr, wc, cl, cr);
+  };
+  solve_tiles(P, X, solve, tile_cost, tile_cover_rows, tile_cover_cols, nnz_row_based);
+  return SHIRO_OK;
+}
+
+extern "C" shiro_status shiro_plan_row_based(shiro_plan_t P, int64_t* tile_rows,
+                                             uint8_t* nnz_row_based, void* stream) {
+  if (!P) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  TileIndex X;
+  SHIRO_TRY(tile_index(P, X, (cudaStream_t)stream));
+  // Every row of a communicated tile that holds a nonzero is selected, no column (Eq. 3).
+  auto solve = [](int32_t, const Bipartite& g, std::vector<char>& cl, std::vector<char>& cr) {
+    cl.assign(g.nL, 0);
+    cr.assign(g.nR, 0);
+    int64_t n = 0;
+    for (int32_t u = 0; u < g.nL; ++u) {
+      cl[u] = g.ptr[u + 1] > g.ptr[u] ? 1 : 0;
+      n += cl[u];
+    }
+    return n;
+  };
+  solve_tiles(P, X, solve, tile_rows, nullptr, nullptr, nnz_row_based);
   return SHIRO_OK;
 }
 

@@ -68,6 +68,8 @@ SIGNATURES = [
     ("shiro_plan_tile_stats", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_volumes", ctypes.c_int, [_vp, _i32, ctypes.c_int, _vp, _vp, _vp]),
     ("shiro_plan_joint", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("shiro_plan_joint_weighted", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]),
+    ("shiro_plan_row_based", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("shiro_joint_split_sizes", ctypes.c_int, [_vp, _vp, _P(_i64), _P(_i64), _P(_i64)]),
     ("shiro_joint_split", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_export", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -268,6 +270,36 @@ class Plan:
         shiro_plan_joint(self.handle, _ptr(mu), _ptr(cr), _ptr(cc), _ptr(side), _stream(stream))
         return {"mu": mu, "cover_rows": cr, "cover_cols": cc, "row_based": side[:n]}
 
+    def joint_weighted(self, w_row=1, w_col=1, stream=None):
+        """Per-tile minimum weighted vertex cover (Sec. 5.3.3 min cut, Dinic).  w_row / w_col are
+        one cost for every row / column, or per-vertex int64 arrays of M / K entries."""
+        T, n = self.info.n_tiles, self.info.nnz
+        cost, cr, cc = (torch.zeros(T, dtype=torch.int64) for _ in range(3))
+        side = torch.zeros(max(n, 1), dtype=torch.uint8)
+
+        def arr(w, size):
+            if isinstance(w, int):
+                return None, w
+            t = torch.as_tensor(w, dtype=torch.int64).contiguous().cpu()
+            if t.numel() != size:
+                raise ValueError(f"expected {size} costs, got {t.numel()}")
+            return t, 0
+
+        wr, wr_all = arr(w_row, self.info.M)
+        wc, wc_all = arr(w_col, self.info.K)
+        shiro_plan_joint_weighted(self.handle, _ptr(wr) if wr is not None else None,
+                                  _ptr(wc) if wc is not None else None, wr_all, wc_all,
+                                  _ptr(cost), _ptr(cr), _ptr(cc), _ptr(side), _stream(stream))
+        return {"cost": cost, "cover_rows": cr, "cover_cols": cc, "row_based": side[:n]}
+
+    def row_based(self, stream=None):
+        """Row-based strategy (Eq. 3): |Rows| per communicated tile and the side of every nonzero."""
+        T, n = self.info.n_tiles, self.info.nnz
+        rows = torch.zeros(T, dtype=torch.int64)
+        side = torch.zeros(max(n, 1), dtype=torch.uint8)
+        shiro_plan_row_based(self.handle, _ptr(rows), _ptr(side), _stream(stream))
+        return {"rows": rows, "row_based": side[:n]}
+
     def export(self, stream=None):
         i = self.info
         d = self.device
@@ -384,12 +416,23 @@ class JointSpMM:
     """C = A B by the joint row-column strategy (Sec. 5.2-5.3): A's tiles are split by a minimum
     vertex cover into column-based nonzeros (packed B rows, plan_col) and row-based ones (partial
     C rows computed where B lives, plan_rs, then added to C in tile order by plan_agg).  All the
-    arithmetic runs in the library; this class only allocates and sequences the calls."""
+    arithmetic runs in the library; this class only allocates and sequences the calls.
+
+    strategy: "joint" (uniform costs, Hopcroft-Karp + Koenig), "weighted" (costs w_row / w_col,
+    min cut by Dinic) or "row" (the row-based strategy of Eq. 3: every communicated nonzero is
+    row-based)."""
 
     def __init__(self, plan: Plan, P_r, P_c, flags=0, row_bounds=None, col_bounds=None,
-                 opts=None):
+                 opts=None, strategy="joint", w_row=1, w_col=1):
         self.base = plan
-        self.cover = plan.joint()
+        if strategy == "joint":
+            self.cover = plan.joint()
+        elif strategy == "weighted":
+            self.cover = plan.joint_weighted(w_row, w_col)
+        elif strategy == "row":
+            self.cover = plan.row_based()
+        else:
+            raise ValueError(f"unknown strategy {strategy!r}")
         side = self.cover["row_based"].contiguous()
         info = plan.info
         dev = plan.device

@@ -1,0 +1,114 @@
+"""Per-tile communication volumes of the four strategies (the volume matrices of Sec. 6.2-6.3).
+
+For every tile A^(p,q) of a plan this reports, in bytes for N columns:
+  V_block  = (width of column block q) * N * sz_B       (Eq. 1, block-based: the whole B block)
+  V_col    = |Cols(A^(p,q))| * N * sz_B                 (Eq. 2, column-based)
+  V_row    = |Rows(A^(p,q))| * N * sz_C                 (Eq. 3, row-based)
+  V_joint  = cost of the minimum weighted vertex cover  (Eq. 9 / Sec. 5.3.3, joint)
+with sz_B the size of a B element and sz_C the size of a partial-C element (FP32 accumulators).
+When sz_B == sz_C the joint cover is the uniform one (Hopcroft-Karp + Koenig) and V_joint =
+mu * N * sz; otherwise it is the min cut with costs N * sz_C per row and N * sz_B per column.
+Local diagonal tiles of a LOCAL_DIAG (1D) plan communicate nothing and report 0 everywhere.
+
+Every number comes from the library (plan statistics and the cover solvers); this module only
+formats them.  Run as ``python -m paper_2512_20178_gb300.volumes --scale 20 --deg 16 --grid 4x4``
+(needs a GPU: the plan is built on the device).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+SIZES = {"f32": 4, "bf16": 2, "f64": 8}
+
+
+def tile_volumes(plan, N: int, b_dtype: str = "f32", c_dtype: str = "f32", local_diag=False):
+    """Per-tile V_block, V_col, V_row and V_joint (int64 arrays of n_tiles) plus the joint cover."""
+    szb, szc = SIZES[b_dtype], SIZES[c_dtype]
+    st = plan.tile_stats()
+    T = plan.info.n_tiles
+    vb, _, _ = plan.volumes(N, {"f32": torch.float32, "bf16": torch.bfloat16,
+                                "f64": torch.float64}[b_dtype])
+    vb = vb.numpy().copy()
+    ncols = st["tile_ncols"].numpy().astype(np.int64)
+    nrows = st["tile_nrows"].numpy().astype(np.int64)
+    if szb == szc:
+        J = plan.joint()
+        vj = J["mu"].numpy().astype(np.int64) * N * szb
+    else:
+        J = plan.joint_weighted(N * szc, N * szb)
+        vj = J["cost"].numpy().astype(np.int64)
+    vc = ncols * N * szb
+    vr = nrows * N * szc
+    if local_diag:
+        Pc = plan.info.P_c
+        for t in range(T):
+            if t // Pc == t % Pc:
+                vb[t] = vc[t] = vr[t] = vj[t] = 0
+    return {"V_block": vb, "V_col": vc, "V_row": vr, "V_joint": vj,
+            "cover_rows": J["cover_rows"].numpy(), "cover_cols": J["cover_cols"].numpy()}
+
+
+def format_matrix(name: str, v: np.ndarray, Pr: int, Pc: int, unit: float = 2**20) -> str:
+    """One volume matrix as text, rows = receiving row block p, columns = sending block q (MiB)."""
+    m = v.reshape(Pr, Pc) / unit
+    w = max(8, max(len(f"{x:.1f}") for x in m.ravel()) + 1)
+    lines = [f"{name} (MiB), row block p x column block q; total {v.sum() / unit:.1f} MiB"]
+    lines.append(" " * 6 + "".join(f"q={q}".rjust(w) for q in range(Pc)))
+    for p in range(Pr):
+        lines.append(f"p={p}".ljust(6) + "".join(f"{x:.1f}".rjust(w) for x in m[p]))
+    return "\n".join(lines)
+
+
+def report(plan, N: int, b_dtype="f32", c_dtype="f32", local_diag=False) -> dict:
+    Pr, Pc = plan.info.P_r, plan.info.P_c
+    V = tile_volumes(plan, N, b_dtype, c_dtype, local_diag)
+    tot = {k: int(V[k].sum()) for k in ("V_block", "V_col", "V_row", "V_joint")}
+    text = "\n\n".join(format_matrix(k, V[k], Pr, Pc) for k in ("V_block", "V_col", "V_row", "V_joint"))
+    red = {"joint_vs_col": 1 - tot["V_joint"] / max(1, tot["V_col"]),
+           "joint_vs_row": 1 - tot["V_joint"] / max(1, tot["V_row"]),
+           "col_vs_block": 1 - tot["V_col"] / max(1, tot["V_block"])}
+    return {"totals": tot, "reductions": red, "text": text,
+            "tiles": {k: V[k].tolist() for k in V}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--graph", choices=["rmat", "er"], default="rmat")
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--deg", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--grid", default="4x4", help="P_r x P_c")
+    ap.add_argument("--local-diag", action="store_true", help="1D: diagonal tiles are local")
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--b-dtype", choices=list(SIZES), default="f32")
+    ap.add_argument("--c-dtype", choices=list(SIZES), default="f32")
+    ap.add_argument("--json", action="store_true")
+    a = ap.parse_args(argv)
+    from . import shiro, synth
+    Pr, Pc = (int(x) for x in a.grid.lower().split("x"))
+    A = synth.rmat(a.scale, a.deg, a.seed) if a.graph == "rmat" else \
+        synth.er(1 << a.scale, a.deg, a.seed)
+    d = torch.device("cuda:0")
+    rp = torch.from_numpy(A.rowptr).to(d)
+    col = torch.from_numpy(A.col).to(d)
+    val = torch.from_numpy(A.val).to(d)
+    flags = shiro.SHIRO_PLAN_LOCAL_DIAG if a.local_diag else 0
+    P = shiro.Plan.create(rp, col, val, A.M, A.K, Pr, Pc, flags=flags)
+    R = report(P, a.N, a.b_dtype, a.c_dtype, a.local_diag)
+    head = {"graph": a.graph, "scale": a.scale, "deg": a.deg, "nnz": int(A.nnz), "grid": a.grid,
+            "local_diag": a.local_diag, "N": a.N, "b_dtype": a.b_dtype, "c_dtype": a.c_dtype}
+    if a.json:
+        print(json.dumps({**head, **{k: R[k] for k in ("totals", "reductions", "tiles")}}))
+    else:
+        print(json.dumps(head))
+        print(R["text"])
+        print(json.dumps({"totals_bytes": R["totals"],
+                          "reductions": {k: round(v, 4) for k, v in R["reductions"].items()}}))
+
+
+if __name__ == "__main__":
+    main()

@@ -134,3 +134,123 @@ def test_joint_spmm_matches_oracle(name, N, dt):
     mu = int(JS.cover["mu"].sum())
     assert sent_b + sent_c == mu, (sent_b, sent_c, mu)
     assert sent_b == int(JS.cover["cover_cols"].sum()) and sent_c == int(JS.cover["cover_rows"].sum())
+
+
+def _weights(A, kind, seed):
+    if kind == "unit":
+        return 1, 1
+    if kind == "bf16_b_fp32_c":
+        # B rows in BF16 (2 bytes) against FP32 partial C rows (4 bytes), N = 64.
+        return 4 * 64, 2 * 64
+    u = synth.uniform_f64(seed, synth.STREAM_VAL, 0, A.M + A.K)
+    return (1 + (u[:A.M] * 20).astype(np.int64)), (1 + (u[A.M:] * 20).astype(np.int64))
+
+
+@pytest.mark.parametrize("name", ["rmat12_4x4", "er4096_1d_local", "ragged_3x5", "hub"])
+@pytest.mark.parametrize("kind", ["unit", "bf16_b_fp32_c", "per_vertex"])
+def test_weighted_cover_matches_oracle(name, kind):
+    """Dinic's min cut in the library against the oracle's (Edmonds-Karp): per tile the same
+    cost, and -- the source-side reachable set being unique -- the same side for every nonzero."""
+    shiro = gu.lib()
+    flags, Pr, Pc = 0, 4, 4
+    if name == "rmat12_4x4":
+        A = synth.rmat(12, 8, 171)
+    elif name == "er4096_1d_local":
+        A, flags = synth.er(4096, 8, 1), shiro.SHIRO_PLAN_LOCAL_DIAG
+    elif name == "ragged_3x5":
+        A, Pr, Pc = synth.random_small(700, 900, 0.01, 172, empty_rows=50), 3, 5
+    else:
+        A, Pr, Pc = synth.hub_matrix(256, 4096, 3, 4000, 2, 173), 2, 2
+    w_row, w_col = _weights(A, kind, 174)
+    P = gu.plan_of(A, Pr, Pc, flags)
+    W = P.joint_weighted(w_row, w_col)
+    O = oracle.plan(A, Pr, Pc)
+    wr = np.full(A.M, w_row, np.int64) if isinstance(w_row, int) else w_row
+    wc = np.full(A.K, w_col, np.int64) if isinstance(w_col, int) else w_col
+    rows = A.row_ids()
+    t_of = (np.searchsorted(O.rb, rows, side="right") - 1) * Pc + \
+        (np.searchsorted(O.cb, A.col, side="right") - 1)
+    side = W["row_based"].numpy()
+    expect_side = np.zeros(A.nnz, np.uint8)
+    for t in range(O.T):
+        p, q = O.tile_pq(t)
+        if flags & shiro.SHIRO_PLAN_LOCAL_DIAG and p == q:
+            assert int(W["cost"][t]) == 0
+            continue
+        nL, nR, ptr, adj = oracle.tile_graph(A, O, t)
+        gcols = O.cols_sorted[O.tile_cols_ptr[t]:O.tile_cols_ptr[t + 1]]
+        flow, cr, cc = oracle.min_weight_cover(nL, nR, ptr, adj, wr[O.rb[p]:O.rb[p + 1]], wc[gcols])
+        assert int(W["cost"][t]) == flow, f"tile {t}: cost {int(W['cost'][t])} != {flow}"
+        assert int(W["cover_rows"][t]) == int(cr.sum()) and int(W["cover_cols"][t]) == int(cc.sum())
+        sel = t_of == t
+        expect_side[sel] = np.where(cc[O.colidx_local[sel]], 0, 1)
+    assert np.array_equal(side, expect_side), "side of some nonzero differs from the oracle's cut"
+    if kind == "unit":
+        J = P.joint()
+        assert np.array_equal(J["mu"].numpy(), W["cost"].numpy())
+        assert np.array_equal(J["row_based"].numpy(), side), "unit costs must give Koenig's cover"
+
+
+def test_row_based_strategy():
+    """Row-based strategy (Eq. 3): every communicated tile sends |Rows| partial C rows and no B
+    row; C through the split equals the oracle's."""
+    shiro = gu.lib()
+    A = synth.rmat(12, 8, 181)
+    for flags in (0, shiro.SHIRO_PLAN_LOCAL_DIAG):
+        P = gu.plan_of(A, 4, 4, flags)
+        R = P.row_based()
+        O = oracle.plan(A, 4, 4)
+        for t in range(O.T):
+            p, q = O.tile_pq(t)
+            expect = 0 if (flags and p == q) else int(O.tile_nrows[t])
+            assert int(R["rows"][t]) == expect
+        JS = shiro.JointSpMM(P, 4, 4, flags=flags, strategy="row")
+        B = synth.dense_normal(A.K, 64, 182)
+        C = JS.spmm(torch.from_numpy(B).to(gu.dev()))
+        torch.cuda.synchronize()
+        gu.check_spmm(A, B, C)
+        sent_b, sent_c = JS.volumes()
+        if not flags:
+            assert sent_b == 0
+        assert sent_c == int(R["rows"].sum())
+
+
+def test_weighted_spmm_bf16_b():
+    """With BF16 B rows (cost 2N) and FP32 partial C rows (cost 4N) the weighted cover is at most
+    as dear as the uniform cover, the column-based and the row-based plans priced the same way,
+    and C through its split matches the oracle."""
+    shiro = gu.lib()
+    A = synth.rmat(13, 8, 191)
+    N = 64
+    P = gu.plan_of(A, 4, 4)
+    W = P.joint_weighted(4 * N, 2 * N)
+    J = P.joint()
+    O = oracle.plan(A, 4, 4)
+    uniform_priced = int((4 * N * J["cover_rows"] + 2 * N * J["cover_cols"]).sum())
+    assert int(W["cost"].sum()) <= uniform_priced
+    assert int(W["cost"].sum()) <= 2 * N * int(O.tile_ncols.sum())
+    assert int(W["cost"].sum()) <= 4 * N * int(O.tile_nrows.sum())
+    JS = shiro.JointSpMM(P, 4, 4, strategy="weighted", w_row=4 * N, w_col=2 * N)
+    B = synth.dense_normal(A.K, N, 192)
+    bits = synth.to_bf16_bits(B)
+    Bh = synth.bf16_bits_to_f32(bits).reshape(B.shape)
+    Bd = torch.from_numpy(bits.view(np.int16)).to(gu.dev()).view(torch.bfloat16)
+    C = JS.spmm(Bd)
+    torch.cuda.synchronize()
+    gu.check_spmm(A, Bh, C)
+    sent_b, sent_c = JS.volumes()
+    assert 2 * N * sent_b + 4 * N * sent_c == int(W["cost"].sum())
+
+
+def test_weighted_cover_rejects_bad_costs():
+    shiro = gu.lib()
+    A = synth.rmat(10, 8, 195)
+    P = gu.plan_of(A, 2, 2)
+    with pytest.raises(shiro.ShiroError):
+        P.joint_weighted(-1, 1)
+    bad = np.ones(A.K, np.int64)
+    bad[3] = -5
+    with pytest.raises(shiro.ShiroError):
+        P.joint_weighted(1, bad)
+    with pytest.raises(ValueError):
+        P.joint_weighted(1, np.ones(A.K + 1, np.int64))

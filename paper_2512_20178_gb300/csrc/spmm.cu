@@ -100,12 +100,15 @@ struct Bases {
   uint32_t ldp, ldb;
 };
 
-template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool LOCAL, bool FULL>
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool LOCAL, bool FULL,
+          bool ENDS = true>
 __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
                                            const Pair<TV>* sp, int n, int off, int32_t r0, int nr,
                                            int rel, unsigned endmask,
                                            typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
   using TA = typename AccOf<TB>::T;
+  // A full batch walks all 32 staged pairs in steps of U without bounds checks.
+  static_assert(32 % U == 0, "U must divide the 32-pair batch");
 #pragma unroll 1
   for (int j = 0; j < (FULL ? 32 : n); j += U) {
     TA b[U][NCH][VEC];
@@ -130,7 +133,7 @@ __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Ba
         for (int c = 0; c < NCH; ++c)
 #pragma unroll
           for (int v = 0; v < VEC; ++v) acc[c][v] = fma((TA)a[u], b[u][c][v], acc[c][v]);
-        if ((endmask >> (j + u)) & 1u) {
+        if (ENDS && ((endmask >> (j + u)) & 1u)) {
           // The nonzero at off + j + u ends a non-empty row: the first lane whose row end is here.
           const unsigned who = __ballot_sync(FULL_MASK, lane < nr && rel == off + j + u + 1);
           flush_row<TV, TB, VEC, NCH, MASKED>(p, r0 + __ffs(who) - 1, acc, lane);
@@ -171,7 +174,12 @@ __device__ __forceinline__ void spmm_span(const SpmmParams<TV, TB>& p, const Bas
     const int q = rel - 1 - off;
     const unsigned bit = (lane < nr && nonempty && q >= 0 && q < 32) ? (1u << q) : 0u;
     const unsigned endmask = __reduce_or_sync(FULL_MASK, bit);
-    if (n == 32)
+    // Full batches with no row end inside (all chunk batches, most batches of long rows) take a
+    // copy of the loop without the flush test: fewer instructions between dependent gathers.
+    if (n == 32 && endmask == 0)
+      spmm_batch<TV, TB, VEC, NCH, MASKED, U, LOCAL, true, false>(p, bs, sp, n, off, r0, nr, rel,
+                                                                  endmask, acc, lane);
+    else if (n == 32)
       spmm_batch<TV, TB, VEC, NCH, MASKED, U, LOCAL, true>(p, bs, sp, n, off, r0, nr, rel, endmask,
                                                            acc, lane);
     else

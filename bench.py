@@ -296,7 +296,10 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks.stop()
     ms = start.elapsed_time(end) / K
-    spmm_ms = sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)) / K
+    launch_ms = sorted(a.elapsed_time(b) for a, b in zip(ev_a, ev_b))
+    spmm_ms = sum(launch_ms) / K
+    pct = lambda q: launch_ms[min(K - 1, int(q * (K - 1) + 0.5))]
+    spmm_stats = {"mean": spmm_ms, "median": pct(0.5), "p10": pct(0.1), "p90": pct(0.9)}
     ms_max = reduce_max(ms, world, dev)
     sp_bytes, pk_bytes = step_bytes(A.M, A.nnz, R, N, sz)
     value = world * (sp_bytes + pk_bytes) / (ms_max * 1e-3) / 1e9
@@ -336,7 +339,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": "k_spmm", "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_from_profile(), "algorithmic_bytes": sp_bytes,
-                "ms_per_launch": spmm_ms}
+                "ms_per_launch": spmm_ms, "launch_ms": spmm_stats}
 
     forms = None
     if not args.no_forms and not bf16:
@@ -355,7 +358,14 @@ def run_ours(args):
     if forms:
         line["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(A, B, args).items() if k != "seconds"}
+        cores = oracle.threads()
+        oracle.set_threads(1)
+        one = cpu_baseline(A, B, args, stride=128)
+        oracle.set_threads(cores)
+        line["cpu_baseline"]["one_thread"] = {"value": one["value"], "unit": "GB/s", "cores": 1,
+                                              "sample": one["sample"]}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -397,7 +407,37 @@ def measure_forms(args, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream, 
     db_ms = timed(lambda: (PT.pack(G, out=Gp), PT.spmm(Gp, out=dB, scratch=sT)))
     da_ms = timed(lambda: P.sddmm(G, Bp, out=dA))
     sddmm_bytes = A.nnz * 8 + A.M * N * 4 + R * N * 4 + A.nnz * 4
-    return {"bf16_B": {"ms": bf16_ms, "GBps": (sp16 + pk16) / (bf16_ms * 1e-3) / 1e9,
+    # N sweep (FP32 B): pack + SpMM and SpMM alone at N = 32 .. 256 on the same plan.
+    n_sweep = {}
+    for n in (32, 64, 128, 256):
+        Bn = torch.from_numpy(synth.dense_normal(A.K, n, 7)).to(dev)
+        Bpn = torch.empty((R, n), dtype=torch.float32, device=dev)
+        Cn = torch.empty((A.M, n), dtype=torch.float32, device=dev)
+        sn = P.new_scratch(n, torch.float32)
+        P.pack(Bn, out=Bpn)
+        spmm_n = timed(lambda: P.spmm(Bpn, out=Cn, scratch=sn))
+        step_n = timed(lambda: (P.pack(Bn, out=Bpn), P.spmm(Bpn, out=Cn, scratch=sn)))
+        spb, pkb = step_bytes(A.M, A.nnz, R, n, 4)
+        n_sweep[str(n)] = {"spmm_ms": spmm_n, "step_ms": step_n,
+                           "spmm_GBps": spb / (spmm_n * 1e-3) / 1e9,
+                           "step_GBps": (spb + pkb) / (step_n * 1e-3) / 1e9}
+        del Bn, Bpn, Cn, sn
+    # Comparator (not on the path): cuSPARSE CSR SpMM through torch.sparse.mm on the unpacked B.
+    cus = None
+    try:
+        At = torch.sparse_csr_tensor(rp.to(torch.int32), col, val, size=(A.M, A.K))
+        Cc = torch.sparse.mm(At, Bd)
+        cus_ms = timed(lambda: torch.sparse.mm(At, Bd))
+        P.pack(Bd, out=Bp)
+        P.spmm(Bp, out=C, scratch=scratch)
+        torch.cuda.synchronize()
+        cus = {"ms": cus_ms, "ours_spmm_ms": timed(lambda: P.spmm(Bp, out=C, scratch=scratch)),
+               "ours_step_ms": fwd_ms, "max_abs_diff": float((Cc - C).abs().max()),
+               "what": "torch.sparse.mm (cuSPARSE CSR SpMM) on the original B, same A, N"}
+        del At, Cc
+    except Exception as e:  # the comparator is optional context
+        cus = {"unavailable": str(e).splitlines()[0][:200]}
+    return {"n_sweep_fp32": n_sweep, "cusparse": cus,"bf16_B": {"ms": bf16_ms, "GBps": (sp16 + pk16) / (bf16_ms * 1e-3) / 1e9,
                        "vs_fp32_speedup": fwd_ms / bf16_ms},
             "fp32_fwd_ms": fwd_ms, "bwd_dB_ms": db_ms, "bwd_dA_ms": da_ms,
             "fwd_bwd_ms": fwd_ms + db_ms + da_ms,

@@ -2,9 +2,10 @@
 // (a sampled dense-dense product on A's pattern, reading B through the packed rows), and the
 // backward entry point that adds dB = A^T dC through the transposed plan.
 //
-// One warp per work item (the SpMM schedule).  For a batch of up to 32 nonzeros every lane
-// forms its slice of the 32 dot products, then a butterfly transpose-reduction (16+8+4+2+1
-// shuffles) leaves the full dot product of nonzero j in lane j, which writes dA coalesced.
+// One warp per work item (the SpMM schedule).  A batch of up to 32 nonzeros is taken as four
+// sub-batches of 8: every lane forms its slice of the 8 dot products, a butterfly reduction
+// (4+2+1 shuffles, then 2) completes them, and one more shuffle hands nonzero j of the batch to
+// lane j, which writes dA coalesced once per batch.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -48,19 +49,25 @@ __device__ __forceinline__ void load_frag(const TB* row, int32_t N, int lane,
   }
 }
 
+// Dot products of 8 nonzeros, lane slices in part[0..7], summed over the warp: a butterfly over
+// lane bits 4, 3, 2 (4 + 2 + 1 shuffles) leaves nonzero (lane >> 2) in every lane, and two more
+// exchanges (lane bits 1, 0) complete its sum.  Eight partials per lane instead of 32.
 template <typename TA>
-__device__ __forceinline__ TA transpose_reduce(TA (&part)[32], int lane) {
+__device__ __forceinline__ TA reduce8(TA (&part)[8], int lane) {
 #pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
+  for (int off = 16, half = 4; off >= 4; off >>= 1, half >>= 1) {
     const bool upper = lane & off;
 #pragma unroll
-    for (int k = 0; k < off; ++k) {
-      const TA send = upper ? part[k] : part[k + off];
-      const TA keep = upper ? part[k + off] : part[k];
+    for (int k = 0; k < half; ++k) {
+      const TA send = upper ? part[k] : part[k + half];
+      const TA keep = upper ? part[k + half] : part[k];
       part[k] = keep + __shfl_xor_sync(FULLM, send, off);
     }
   }
-  return part[0];
+  TA r = part[0];
+  r += __shfl_xor_sync(FULLM, r, 2);
+  r += __shfl_xor_sync(FULLM, r, 1);
+  return r;
 }
 
 // Row of the stream position `pos` (relative to the item start) and the next non-empty row after
@@ -105,46 +112,54 @@ __device__ __forceinline__ void sddmm_item(const SddmmParams<TB>& p, int32_t* s_
     const int q = rel - 1 - off;
     const unsigned bit = (lane < nr && nonempty && q >= 0 && q < 32) ? (1u << q) : 0u;
     const unsigned endmask = __reduce_or_sync(FULLM, bit);
-    TA part[32];
+    // Four sub-batches of 8 nonzeros; lane l keeps the result of nonzero off + l.
+    TA out = 0;
+#pragma unroll 1
+    for (int sb = 0; sb < n; sb += 8) {
+      TA part[8];
 #pragma unroll
-    for (int j = 0; j < 32; j += U) {
-      TA b[U][NCH][VEC];
+      for (int j = 0; j < 8; j += U) {
+        TA b[U][NCH][VEC];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (j + u < n) {
-          const int32_t idx = s_idx[j + u];
-          const TB* row = idx >= 0 ? p.Bpack + (uint64_t)(uint32_t)idx * (uint32_t)p.ldp
-                                   : p.B + (uint64_t)(uint32_t)(-1 - idx) * (uint32_t)p.ldb;
-          load_frag<TB, VEC, NCH, MASKED>(row, p.N, lane, b[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        TA s = 0;
-        if (j + u < n) {
-#pragma unroll
-          for (int c = 0; c < NCH; ++c)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) s = fma(g[c][v], b[u][c][v], s);
-          if ((endmask >> (j + u)) & 1u) {
-            // The stream leaves row r0 + cur here: move to the prefetched next row.
-            cur = nxt;
-            if (cur >= 0) {
-#pragma unroll
-              for (int c = 0; c < NCH; ++c)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) g[c][v] = gn[c][v];
-              nxt = next_nonempty_row(rel, nonempty, nr, __shfl_sync(FULLM, rel, cur), lane);
-              if (nxt >= 0)
-                load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + nxt) * p.lddc, p.N, lane, gn);
-            }
+        for (int u = 0; u < U; ++u) {
+          if (sb + j + u < n) {
+            const int32_t idx = s_idx[sb + j + u];
+            const TB* row = idx >= 0 ? p.Bpack + (uint64_t)(uint32_t)idx * (uint32_t)p.ldp
+                                     : p.B + (uint64_t)(uint32_t)(-1 - idx) * (uint32_t)p.ldb;
+            load_frag<TB, VEC, NCH, MASKED>(row, p.N, lane, b[u]);
           }
         }
-        part[j + u] = s;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          TA s = 0;
+          if (sb + j + u < n) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) s = fma(g[c][v], b[u][c][v], s);
+            if ((endmask >> (sb + j + u)) & 1u) {
+              // The stream leaves row r0 + cur here: move to the prefetched next row.
+              cur = nxt;
+              if (cur >= 0) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                  for (int v = 0; v < VEC; ++v) g[c][v] = gn[c][v];
+                nxt = next_nonempty_row(rel, nonempty, nr, __shfl_sync(FULLM, rel, cur), lane);
+                if (nxt >= 0)
+                  load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + nxt) * p.lddc, p.N, lane,
+                                                  gn);
+              }
+            }
+          }
+          part[j + u] = s;
+        }
       }
+      const TA r = reduce8<TA>(part, lane);
+      const TA v = __shfl_sync(FULLM, r, (lane & 7) << 2);
+      if ((lane >> 3) == (sb >> 3)) out = v;
     }
-    const TA tot = transpose_reduce<TA>(part, lane);
-    if (lane < n) p.dA[item.e0 + off + lane] = tot;
+    if (lane < n) p.dA[item.e0 + off + lane] = out;
   }
 }
 

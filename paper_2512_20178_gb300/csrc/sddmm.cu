@@ -78,6 +78,65 @@ __device__ __forceinline__ int next_nonempty_row(int rel, bool nonempty, int nr,
   return m ? __ffs(m) - 1 : -1;
 }
 
+// One batch of up to 32 staged nonzeros as four sub-batches of 8; returns, in lane l, the dot
+// product of nonzero l of the batch.  cur / nxt and g / gn track the current and the next
+// non-empty row and their dC slices across row ends.
+template <typename TB, int VEC, int NCH, bool MASKED, int U, bool FULL, bool ENDS>
+__device__ __forceinline__ typename AccOf<TB>::T sddmm_batch(
+    const SddmmParams<TB>& p, const int32_t* s_idx, int n, unsigned endmask, int32_t r0, int nr,
+    int rel, bool nonempty, int& cur, int& nxt, typename AccOf<TB>::T (&g)[NCH][VEC],
+    typename AccOf<TB>::T (&gn)[NCH][VEC], int lane) {
+  using TA = typename AccOf<TB>::T;
+  static_assert(8 % U == 0, "U must divide the 8-nonzero sub-batch");
+  TA out = 0;
+#pragma unroll 1
+  for (int sb = 0; sb < (FULL ? 32 : n); sb += 8) {
+    TA part[8];
+#pragma unroll
+    for (int j = 0; j < 8; j += U) {
+      TA b[U][NCH][VEC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (FULL || sb + j + u < n) {
+          const int32_t idx = s_idx[sb + j + u];
+          const TB* row = idx >= 0 ? p.Bpack + (uint64_t)(uint32_t)idx * (uint32_t)p.ldp
+                                   : p.B + (uint64_t)(uint32_t)(-1 - idx) * (uint32_t)p.ldb;
+          load_frag<TB, VEC, NCH, MASKED>(row, p.N, lane, b[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        TA s = 0;
+        if (FULL || sb + j + u < n) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s = fma(g[c][v], b[u][c][v], s);
+          if (ENDS && ((endmask >> (sb + j + u)) & 1u)) {
+            // The stream leaves row r0 + cur here: move to the prefetched next row.
+            cur = nxt;
+            if (cur >= 0) {
+#pragma unroll
+              for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) g[c][v] = gn[c][v];
+              nxt = next_nonempty_row(rel, nonempty, nr, __shfl_sync(FULLM, rel, cur), lane);
+              if (nxt >= 0)
+                load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + nxt) * p.lddc, p.N, lane,
+                                                gn);
+            }
+          }
+        }
+        part[j + u] = s;
+      }
+    }
+    const TA r = reduce8<TA>(part, lane);
+    const TA v = __shfl_sync(FULLM, r, (lane & 7) << 2);
+    if ((lane >> 3) == (sb >> 3)) out = v;
+  }
+  return out;
+}
+
 template <typename TB, int VEC, int NCH, bool MASKED, int U>
 __device__ __forceinline__ void sddmm_item(const SddmmParams<TB>& p, int32_t* s_idx,
                                            const Item& item, int lane) {
@@ -112,53 +171,12 @@ __device__ __forceinline__ void sddmm_item(const SddmmParams<TB>& p, int32_t* s_
     const int q = rel - 1 - off;
     const unsigned bit = (lane < nr && nonempty && q >= 0 && q < 32) ? (1u << q) : 0u;
     const unsigned endmask = __reduce_or_sync(FULLM, bit);
-    // Four sub-batches of 8 nonzeros; lane l keeps the result of nonzero off + l.
-    TA out = 0;
-#pragma unroll 1
-    for (int sb = 0; sb < n; sb += 8) {
-      TA part[8];
-#pragma unroll
-      for (int j = 0; j < 8; j += U) {
-        TA b[U][NCH][VEC];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (sb + j + u < n) {
-            const int32_t idx = s_idx[sb + j + u];
-            const TB* row = idx >= 0 ? p.Bpack + (uint64_t)(uint32_t)idx * (uint32_t)p.ldp
-                                     : p.B + (uint64_t)(uint32_t)(-1 - idx) * (uint32_t)p.ldb;
-            load_frag<TB, VEC, NCH, MASKED>(row, p.N, lane, b[u]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          TA s = 0;
-          if (sb + j + u < n) {
-#pragma unroll
-            for (int c = 0; c < NCH; ++c)
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) s = fma(g[c][v], b[u][c][v], s);
-            if ((endmask >> (sb + j + u)) & 1u) {
-              // The stream leaves row r0 + cur here: move to the prefetched next row.
-              cur = nxt;
-              if (cur >= 0) {
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-#pragma unroll
-                  for (int v = 0; v < VEC; ++v) g[c][v] = gn[c][v];
-                nxt = next_nonempty_row(rel, nonempty, nr, __shfl_sync(FULLM, rel, cur), lane);
-                if (nxt >= 0)
-                  load_frag<TB, VEC, NCH, MASKED>(p.dC + (int64_t)(r0 + nxt) * p.lddc, p.N, lane,
-                                                  gn);
-              }
-            }
-          }
-          part[j + u] = s;
-        }
-      }
-      const TA r = reduce8<TA>(part, lane);
-      const TA v = __shfl_sync(FULLM, r, (lane & 7) << 2);
-      if ((lane >> 3) == (sb >> 3)) out = v;
-    }
+    // Full batches with no row end inside take a copy of the loop without per-nonzero tests.
+    const TA out = (n == 32 && endmask == 0)
+        ? sddmm_batch<TB, VEC, NCH, MASKED, U, true, false>(p, s_idx, n, endmask, r0, nr, rel,
+                                                            nonempty, cur, nxt, g, gn, lane)
+        : sddmm_batch<TB, VEC, NCH, MASKED, U, false, true>(p, s_idx, n, endmask, r0, nr, rel,
+                                                            nonempty, cur, nxt, g, gn, lane);
     if (lane < n) p.dA[item.e0 + off + lane] = out;
   }
 }

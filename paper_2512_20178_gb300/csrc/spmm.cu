@@ -70,6 +70,22 @@ __device__ __forceinline__ void gather_row(const SpmmParams<TV, TB>& p, const TB
 }
 
 template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
+__device__ __forceinline__ void gather_raw(
+    const SpmmParams<TV, TB>& p, const TB* row,
+    typename RawFrag<TB, VEC>::T (&b)[NCH][RawFrag<TB, VEC>::W], int lane) {
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    const int col = c * 32 * VEC + lane * VEC;
+    if (!MASKED || col < p.N) {
+      load_raw<TB, VEC>(row + c * 32 * VEC, b[c]);
+    } else {
+#pragma unroll
+      for (int w = 0; w < RawFrag<TB, VEC>::W; ++w) b[c][w] = 0;
+    }
+  }
+}
+
+template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
 __device__ __forceinline__ void flush_row(const SpmmParams<TV, TB>& p, int32_t r,
                                           typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
   using TA = typename AccOf<TB>::T;
@@ -111,7 +127,7 @@ __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Ba
   static_assert(32 % U == 0, "U must divide the 32-pair batch");
 #pragma unroll 1
   for (int j = 0; j < (FULL ? 32 : n); j += U) {
-    TA b[U][NCH][VEC];
+    typename RawFrag<TB, VEC>::T b[U][NCH][RawFrag<TB, VEC>::W];
     TV a[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -123,16 +139,14 @@ __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Ba
           row = bs.b + (uint64_t)(uint32_t)(-1 - pr.idx) * bs.ldb;
         else
           row = bs.bp + (uint64_t)(uint32_t)pr.idx * bs.ldp;
-        gather_row<TV, TB, VEC, NCH, MASKED>(p, row, b[u], lane);
+        gather_raw<TV, TB, VEC, NCH, MASKED>(p, row, b[u], lane);
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (FULL || j + u < n) {
 #pragma unroll
-        for (int c = 0; c < NCH; ++c)
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) acc[c][v] = fma((TA)a[u], b[u][c][v], acc[c][v]);
+        for (int c = 0; c < NCH; ++c) fma_raw<TB, VEC>(a[u], b[u][c], acc[c]);
         if (ENDS && ((endmask >> (j + u)) & 1u)) {
           // The nonzero at off + j + u ends a non-empty row: the first lane whose row end is here.
           const unsigned who = __ballot_sync(FULL_MASK, lane < nr && rel == off + j + u + 1);
@@ -288,15 +302,22 @@ namespace shiro {
 
 template <int VEC, int NCH, typename TB>
 struct Occupancy {
-  // Registers per lane held by one gathered row fragment.
-  static constexpr int REG = VEC * NCH * (int)(sizeof(typename AccOf<TB>::T) / 4);
+  // Registers per lane held by one gathered row fragment in flight (raw storage words).
+  static constexpr int REG =
+      RawFrag<TB, VEC>::W * NCH * (int)((sizeof(typename RawFrag<TB, VEC>::T) + 3) / 4);
 #ifndef SHIRO_SPMM_U
 #define SHIRO_SPMM_U 4
 #endif
 #ifndef SHIRO_SPMM_U8
 #define SHIRO_SPMM_U8 2
 #endif
-  static constexpr int U = REG >= 16 ? 2 : (REG >= 8 ? SHIRO_SPMM_U8 : SHIRO_SPMM_U);
+#ifndef SHIRO_SPMM_UW
+#define SHIRO_SPMM_UW 2
+#endif
+  // Accumulators wider than one 4-register fragment (BF16 rows of 256 elements).
+  static constexpr bool WIDE_ACC = VEC * NCH * (int)(sizeof(typename AccOf<TB>::T) / 4) > 4;
+  static constexpr int U =
+      REG >= 16 ? 2 : (REG >= 8 ? SHIRO_SPMM_U8 : (WIDE_ACC ? SHIRO_SPMM_UW : SHIRO_SPMM_U));
   // 64 registers for 4-register fragments (32 warps per SM): measured faster than 80 registers
   // without spills (24 warps), though ptxas spills a few bytes of the long-row epilogue.
 #ifndef SHIRO_SPMM_MIN_BLOCKS

@@ -56,6 +56,57 @@ __device__ __forceinline__ void load_vec(const TB* p, typename AccOf<TB>::T (&ou
   }
 }
 
+// Raw storage words of a VEC-element fragment, kept as loaded while the gather is in flight:
+// the elements themselves for FP32 / FP64, packed BF16 pairs for BF16 (VEC / 2 words; one
+// half-word in the low bits for VEC = 1), widened only where they are consumed, so a BF16 row
+// in flight costs half the registers of its FP32 widening.
+template <typename TB, int VEC> struct RawFrag {
+  using T = TB;
+  static constexpr int W = VEC;
+};
+template <int VEC> struct RawFrag<__nv_bfloat16, VEC> {
+  using T = uint32_t;
+  static constexpr int W = (VEC + 1) / 2;
+};
+
+template <typename TB, int VEC>
+__device__ __forceinline__ void load_raw(const TB* p,
+                                         typename RawFrag<TB, VEC>::T (&w)[RawFrag<TB, VEC>::W]) {
+  if constexpr (!std::is_same<TB, __nv_bfloat16>::value) {
+    load_vec<TB, VEC, true>(p, w);
+  } else if constexpr (VEC == 8) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else if constexpr (VEC == 4) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    w[0] = v.x; w[1] = v.y;
+  } else if constexpr (VEC == 2) {
+    w[0] = __ldg(reinterpret_cast<const unsigned int*>(p));
+  } else {
+    w[0] = __ldg(reinterpret_cast<const unsigned short*>(p));
+  }
+}
+
+// acc[v] = fma(a, element v of the raw fragment, acc[v]) for v = 0 .. VEC-1, in that order (the
+// BF16 widening is exact, so this equals widening first).
+template <typename TB, int VEC, typename TV>
+__device__ __forceinline__ void fma_raw(TV a, const typename RawFrag<TB, VEC>::T (&w)[RawFrag<TB, VEC>::W],
+                                        typename AccOf<TB>::T (&acc)[VEC]) {
+  using TA = typename AccOf<TB>::T;
+  if constexpr (!std::is_same<TB, __nv_bfloat16>::value) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = fma((TA)a, w[v], acc[v]);
+  } else if constexpr (VEC == 1) {
+    acc[0] = fma((TA)a, bf16_lo(w[0]), acc[0]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC / 2; ++k) {
+      acc[2 * k] = fma((TA)a, bf16_lo(w[k]), acc[2 * k]);
+      acc[2 * k + 1] = fma((TA)a, bf16_hi(w[k]), acc[2 * k + 1]);
+    }
+  }
+}
+
 // Store VEC accumulator values (float or double) at p; STREAM uses an evict-first store.
 template <typename TA, int VEC, bool STREAM>
 __device__ __forceinline__ void store_vec(TA* p, const TA (&v)[VEC]) {

@@ -48,6 +48,7 @@ struct SpmmParams {
   int32_t accumulate;
   int32_t persistent;
   int* status;
+  int32_t pf_bytes;  // bytes of a row to prefetch into L2 ahead of its gather (0: off)
 };
 
 // (index, value) of one nonzero as staged in shared memory; two FP32 entries fill 16 bytes.
@@ -141,6 +142,20 @@ __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Ba
           row = bs.bp + (uint64_t)(uint32_t)pr.idx * bs.ldp;
         gather_raw<TV, TB, VEC, NCH, MASKED>(p, row, b[u], lane);
       }
+    }
+#ifndef SHIRO_SPMM_PF
+#define SHIRO_SPMM_PF 2
+#endif
+    // Rows of 512 bytes or more (16 bytes per lane and up): bring the rows of the step
+    // SHIRO_SPMM_PF steps ahead into L2 while this step's gathers are in flight (more requests
+    // outstanding to HBM without registers).  Narrower rows are bound by instructions, not by
+    // misses, and skip it.
+    constexpr bool PF = VEC * NCH * sizeof(TB) >= 16;
+    if (PF && FULL && p.pf_bytes && j + SHIRO_SPMM_PF * U < 32 && lane < U) {
+      const int32_t ix = sp[j + SHIRO_SPMM_PF * U + lane].idx;
+      const TB* r = (LOCAL && ix < 0) ? p.B + (uint64_t)(uint32_t)(-1 - ix) * (uint64_t)p.ldb
+                                      : p.Bpack + (uint64_t)(uint32_t)ix * (uint64_t)p.ldp;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(r), "r"(p.pf_bytes));
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -600,6 +615,13 @@ static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t
   prm.accumulate = (flags & SHIRO_SPMM_ACCUMULATE) ? 1 : 0;
   prm.persistent = P->opts.persistent;
   prm.status = P->d_status;
+  {
+    const size_t rb = (size_t)N * dtype_size(dt);
+    const bool al16 = ((uintptr_t)Bpack % 16) == 0 && ((size_t)ldp * dtype_size(dt)) % 16 == 0 &&
+                      (!(P->flags & SHIRO_PLAN_LOCAL_DIAG) ||
+                       (((uintptr_t)B % 16) == 0 && ((size_t)ldb * dtype_size(dt)) % 16 == 0));
+    prm.pf_bytes = (rb % 16 == 0 && rb > 0 && rb <= (1u << 20) && al16) ? (int32_t)rb : 0;
+  }
   const size_t esz = dtype_size(dt);
   const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
   auto ok = [&](int vec) {

@@ -173,6 +173,18 @@ def traffic_from_profile():
     return rec.get("dram_bytes_per_launch")
 
 
+def cpu_model() -> str:
+    """Host CPU model as lscpu reports it (empty if unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for line in out.splitlines():
+        if line.strip().lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    return ""
+
+
 def cpu_baseline(A, B, args, stride=8):
     """The FP64 oracle (pack + SpMM through the packed rows) on every stride-th row of A."""
     import oracle
@@ -193,6 +205,7 @@ def cpu_baseline(A, B, args, stride=8):
     sp, pk = step_bytes(S.M, S.nnz, len(src), args.N, 4)
     gbs = (sp + pk) / (t2 - t1) / 1e9
     return {"value": gbs, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "sample": f"every {stride}th row ({S.M} rows, {S.nnz} nnz), pack + SpMM via packed "
                       f"rows in FP64; plan {t1 - t0:.2f} s not counted",
             "seconds": t2 - t1}
@@ -223,7 +236,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded R-MAT)", "config": config(args, A),
-            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model", "nproc")},
             "e2e": {"value": res["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

@@ -122,7 +122,8 @@ template <typename TV, typename TB, int VEC, int NCH, bool MASKED, int U, bool L
 __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
                                            const Pair<TV>* sp, int n, int off, int32_t r0, int nr,
                                            int rel, unsigned endmask,
-                                           typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
+                                           typename AccOf<TB>::T (&acc)[NCH][VEC], int lane,
+                                           int32_t nidx = 0, int nnext = 0) {
   using TA = typename AccOf<TB>::T;
   // A full batch walks all 32 staged pairs in steps of U without bounds checks.
   static_assert(32 % U == 0, "U must divide the 32-pair batch");
@@ -151,11 +152,26 @@ __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Ba
     // outstanding to HBM without registers).  Narrower rows are bound by instructions, not by
     // misses, and skip it.
     constexpr bool PF = VEC * NCH * sizeof(TB) >= 16;
-    if (PF && FULL && p.pf_bytes && j + SHIRO_SPMM_PF * U < 32 && lane < U) {
-      const int32_t ix = sp[j + SHIRO_SPMM_PF * U + lane].idx;
-      const TB* r = (LOCAL && ix < 0) ? p.B + (uint64_t)(uint32_t)(-1 - ix) * (uint64_t)p.ldb
-                                      : p.Bpack + (uint64_t)(uint32_t)ix * (uint64_t)p.ldp;
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(r), "r"(p.pf_bytes));
+    // BF16 rows (raw words in flight leave registers free) also prefetch across the batch end,
+    // from the next batch's indices (one per lane in nidx); FP32 rows would spill for it.
+    constexpr bool XB = PF && std::is_same<TB, __nv_bfloat16>::value;
+    if (PF && FULL && p.pf_bytes) {
+      const int k = j + SHIRO_SPMM_PF * U;
+      if (k < 32) {
+        if (lane < U) {
+          const int32_t ix = sp[k + lane].idx;
+          const TB* r = (LOCAL && ix < 0) ? p.B + (uint64_t)(uint32_t)(-1 - ix) * (uint64_t)p.ldb
+                                          : p.Bpack + (uint64_t)(uint32_t)ix * (uint64_t)p.ldp;
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(r), "r"(p.pf_bytes));
+        }
+      } else if (XB) {
+        const int32_t ix = __shfl_sync(FULL_MASK, nidx, (k - 32) + (lane & (U - 1)));
+        if (lane < U && (k - 32) + lane < nnext) {
+          const TB* r = (LOCAL && ix < 0) ? p.B + (uint64_t)(uint32_t)(-1 - ix) * (uint64_t)p.ldb
+                                          : p.Bpack + (uint64_t)(uint32_t)ix * (uint64_t)p.ldp;
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(r), "r"(p.pf_bytes));
+        }
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -207,10 +223,11 @@ __device__ __forceinline__ void spmm_span(const SpmmParams<TV, TB>& p, const Bas
     // copy of the loop without the flush test: fewer instructions between dependent gathers.
     if (n == 32 && endmask == 0)
       spmm_batch<TV, TB, VEC, NCH, MASKED, U, LOCAL, true, false>(p, bs, sp, n, off, r0, nr, rel,
-                                                                  endmask, acc, lane);
+                                                                  endmask, acc, lane, nidx,
+                                                                  total - off - 32);
     else if (n == 32)
       spmm_batch<TV, TB, VEC, NCH, MASKED, U, LOCAL, true>(p, bs, sp, n, off, r0, nr, rel, endmask,
-                                                           acc, lane);
+                                                           acc, lane, nidx, total - off - 32);
     else
       spmm_batch<TV, TB, VEC, NCH, MASKED, U, LOCAL, false>(p, bs, sp, n, off, r0, nr, rel,
                                                             endmask, acc, lane);

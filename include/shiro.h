@@ -327,7 +327,8 @@ shiro_status shiro_autotune(shiro_plan_t plan, const void* Bpack, int64_t ldp, c
  * compute calls use the thread's current device; streams passed in must belong to it. */
 shiro_status shiro_set_device(int32_t device);
 
-/* Default schedule options. */
+/* Default schedule options: long_row_nnz 512, chunk_nnz 256, group_nnz 256, group_rows 32,
+ * warps_per_cta 1, persistent 0, pipeline 0, stage_rows 0. */
 void shiro_default_opts(shiro_opts* opts);
 
 /* Thread-local message of the last error. */

@@ -147,23 +147,25 @@ __device__ __forceinline__ void spmm_batch(const SpmmParams<TV, TB>& p, const Ba
 #ifndef SHIRO_SPMM_PF
 #define SHIRO_SPMM_PF 2
 #endif
-    // Rows of 512 bytes or more (16 bytes per lane and up): bring the rows of the step
-    // SHIRO_SPMM_PF steps ahead into L2 while this step's gathers are in flight (more requests
-    // outstanding to HBM without registers).  Narrower rows are bound by instructions, not by
-    // misses, and skip it.
-    constexpr bool PF = VEC * NCH * sizeof(TB) >= 16;
+    // Kernels that keep only U <= 2 rows of 512 bytes or more in flight per warp (FP32 N >= 256,
+    // BF16 N = 256): bring the rows of the step SHIRO_SPMM_PF steps ahead into L2 while this
+    // step's gathers are in flight (more requests outstanding to HBM without registers).  With
+    // U = 4 the prefetch code costs more issue slots than the misses it hides (measured).
+    constexpr bool PF = VEC * NCH * sizeof(TB) >= 16 && U <= 2;
     // BF16 rows (raw words in flight leave registers free) also prefetch across the batch end,
     // from the next batch's indices (one per lane in nidx); FP32 rows would spill for it.
     constexpr bool XB = PF && std::is_same<TB, __nv_bfloat16>::value;
     if (PF && FULL && p.pf_bytes) {
       const int k = j + SHIRO_SPMM_PF * U;
       if (k < 32) {
-        if (lane < U) {
-          const int32_t ix = sp[k + lane].idx;
-          const TB* r = (LOCAL && ix < 0) ? p.B + (uint64_t)(uint32_t)(-1 - ix) * (uint64_t)p.ldb
-                                          : p.Bpack + (uint64_t)(uint32_t)ix * (uint64_t)p.ldp;
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(r), "r"(p.pf_bytes));
-        }
+        // Every lane forms an address; lanes 0 .. U-1 issue (predicated, no branch).
+        const int32_t ix = sp[k + (lane & (U - 1))].idx;
+        const TB* r = (LOCAL && ix < 0) ? p.B + (uint64_t)(uint32_t)(-1 - ix) * (uint64_t)p.ldb
+                                        : p.Bpack + (uint64_t)(uint32_t)ix * (uint64_t)p.ldp;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.lt.u32 q, %2, %3;\n\t"
+            "@q cp.async.bulk.prefetch.L2.global [%0], %1;\n\t}"
+            ::"l"(r), "r"(p.pf_bytes), "r"(lane), "r"(U));
       } else if (XB) {
         const int32_t ix = __shfl_sync(FULL_MASK, nidx, (k - 32) + (lane & (U - 1)));
         if (lane < U && (k - 32) + lane < nnext) {

@@ -94,14 +94,26 @@ typedef struct {
   int32_t group_rows;
   int32_t warps_per_cta; /* 1..8 */
   int32_t persistent;    /* 1: grid = SMs x resident CTAs and warps stride over the items */
-  int32_t pipeline;      /* 0: B-row gathers into registers; 1: staged through shared memory by
-                            per-lane asynchronous copies; 2: staged by one TMA bulk copy per row
-                            (rows of a multiple of 16 bytes, 16-byte aligned; else 1) --
-                            two stages per warp for 1 and 2; 3: rows of 128 or 256 bytes (FP32
-                            N = 32/64, BF16 N = 64/128) split across 4 or 2 lane groups that take
-                            interleaved nonzeros of a row (other rows as 0) */
-  int32_t stage_rows;    /* rows per stage with pipeline 1: 8, 16 or 32 (0 = the largest that keeps
-                            a stage within 16 KB) */
+  int32_t pipeline;      /* How the gathered B rows reach the accumulators (every pipeline sums
+                            a row's nonzeros in the same order, except 3):
+                            0: automatic -- 5 for rows below 1 KB, 4 for FP32/BF16 rows of
+                               1-2 KB (the faster of the two there, measured);
+                            1: staged through shared memory by per-lane asynchronous copies, two
+                               stages per warp;
+                            2: staged by one TMA bulk copy per row, two stages per warp (rows of
+                               a multiple of 16 bytes, 16-byte aligned; else 1);
+                            3: rows of 128 or 256 bytes (FP32 N = 32/64, BF16 N = 64/128) split
+                               across 4 or 2 lane groups that take interleaved nonzeros of a row
+                               (other rows as 0);
+                            4: a per-warp ring of row slots refilled by per-lane asynchronous
+                               copies stage_rows rows ahead (FP32/BF16 rows of 256 bytes to 2 KB;
+                               else 5);
+                            5: register gathers, 2-4 rows in flight per warp */
+  int32_t stage_rows;    /* pipeline 1: rows per stage, 8, 16 or 32 (0 = the largest that keeps a
+                            stage within 16 KB); pipeline 4: ring depth, 16 or 32 for 256-byte
+                            rows (0 = 16), 8, 12 or 16 for 512-byte rows (0 = 8), 4 or 8 for
+                            1-2 KB rows (0 = 4).  Accepted values: 0, 4, 8, 12, 16, 32; a ring
+                            depth not compiled for the row size takes its default */
 } shiro_opts;
 
 /* Bytes of workspace shiro_plan_create needs for A and this partition (an upper bound that does
@@ -314,8 +326,9 @@ shiro_status shiro_batch_plan_create(int32_t G, const shiro_csr* graphs, const s
 /* Autotuner: times shiro_spmm over a set of candidate schedules on the caller's operands (Bpack,
  * C and scratch as for shiro_spmm; C is overwritten) and leaves the fastest one in the plan
  * (*best receives it).  Candidates vary the row-group size (from the average row length), the
- * chunk size of long rows (only when some row is longer), the CTA size and, for rows of 128 or
- * 256 bytes, the lane-group pipeline; the persistent mode stays as set.  Candidates whose scratch
+ * chunk size of long rows (only when some row is longer), the CTA size and the pipeline: register
+ * gathers, plus lane groups for rows of 128 or 256 bytes and the per-lane copy ring for FP32/BF16
+ * rows of 512 bytes to 2 KB; the persistent mode stays as set.  Candidates whose scratch
  * does not fit scratch_bytes are skipped.  Synchronises `stream`. */
 shiro_status shiro_autotune(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
                             int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,

@@ -331,6 +331,7 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Bas
 #include "spmm_async.cuh"
 #include "spmm_bulk.cuh"
 #include "spmm_grouped.cuh"
+#include "spmm_ring.cuh"
 
 namespace shiro {
 
@@ -550,13 +551,72 @@ static shiro_status launch_bulk(const shiro_plan_s* P, const SpmmParams<TV, TB>&
   return launch_bulk_batch<TV, TB, VEC, NCH, 8>(P, prm, s);
 }
 
+template <typename TV, typename TB, int VEC, int NCH, int R, int G>
+static shiro_status launch_lring_rg(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                    cudaStream_t s) {
+  using L = LRingLayout<TV, TB, VEC, NCH, R, G>;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm_lring<TV, TB, VEC, NCH, R, G, true>
+                    : k_spmm_lring<TV, TB, VEC, NCH, R, G, false>;
+  const int max_smem = 227 * 1024;
+  const int wpc = std::max(1, std::min(P->opts.warps_per_cta, max_smem / L::WARP));
+  const int smem = wpc * L::WARP;
+  SHIRO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.chunk_blocks = (q.n_chunk_items + wpc - 1) / wpc;
+  const int64_t n_groups = prm.n_items - q.n_chunk_items;
+  int64_t gblocks = (n_groups + wpc - 1) / wpc;
+  if (prm.persistent) {
+    int per_sm = 0;
+    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, smem));
+    gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
+  }
+  const int64_t grid = q.chunk_blocks + gblocks;
+  if (grid <= 0) return SHIRO_OK;
+  if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+  kern<<<(unsigned)grid, wpc * 32, smem, s>>>(q);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
+// Ring depths compiled per row size: 256-byte rows keep 16 or 32 rows (default 16),
+// 512-byte rows 8, 12 or 16 (default 8), rows of 1-2 KB 4 or 8 in groups of 2 (default 4).
+template <typename TV, typename TB, int VEC, int NCH>
+static shiro_status launch_lring(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                 cudaStream_t s) {
+  constexpr int ROW = 32 * VEC * NCH * (int)sizeof(TB);
+  const int want = P->opts.stage_rows;
+  if constexpr (ROW == 256) {
+    if (want == 32) return launch_lring_rg<TV, TB, VEC, NCH, 32, 4>(P, prm, s);
+    return launch_lring_rg<TV, TB, VEC, NCH, 16, 4>(P, prm, s);
+  } else if constexpr (ROW == 512) {
+    if (want == 12) return launch_lring_rg<TV, TB, VEC, NCH, 12, 4>(P, prm, s);
+    if (want == 16) return launch_lring_rg<TV, TB, VEC, NCH, 16, 4>(P, prm, s);
+    return launch_lring_rg<TV, TB, VEC, NCH, 8, 4>(P, prm, s);
+  } else {
+    if (want == 8) return launch_lring_rg<TV, TB, VEC, NCH, 8, 2>(P, prm, s);
+    return launch_lring_rg<TV, TB, VEC, NCH, 4, 2>(P, prm, s);
+  }
+}
+
 template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
                                cudaStream_t s) {
   if constexpr (!MASKED && VEC * sizeof(TB) >= 4) {
+    constexpr int ROW = 32 * VEC * NCH * (int)sizeof(TB);
+    // Per-lane copy ring (pipeline 4) for FP32 / BF16 rows of 256 bytes to 2 KB; with pipeline 0
+    // (automatic) rows of 1 KB or more take it (measured faster than register gathers there,
+    // slower below).  Pipeline 5 forces register gathers.
+    if constexpr (!std::is_same<TB, double>::value && ROW >= 256 && ROW <= 2048 &&
+                  (ROW & (ROW - 1)) == 0) {
+      if (P->opts.pipeline == 4 || (P->opts.pipeline == 0 && ROW >= 1024))
+        return launch_lring<TV, TB, VEC, NCH>(P, prm, s);
+    }
     if (P->opts.pipeline == 2 && bulk_ok<TV, TB, VEC, NCH>(P, prm))
       return launch_bulk<TV, TB, VEC, NCH>(P, prm, s);
-    if (P->opts.pipeline) return launch_async<TV, TB, VEC, NCH>(P, prm, s);
+    if (P->opts.pipeline == 1 || P->opts.pipeline == 2)
+      return launch_async<TV, TB, VEC, NCH>(P, prm, s);
   }
   constexpr int U = Occupancy<VEC, NCH, TB>::U;
   const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
@@ -721,10 +781,13 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
   const int32_t groups[] = {128, 256, 512, 1024};
   const int32_t chunks[] = {256, 512, 1024};
   const int32_t warps[] = {1, 2, 4};
-  // Pipelines worth trying: register gathers, and lane groups when rows are 128 or 256 bytes.
+  // Pipelines worth trying: register gathers (5), lane groups when rows are 128 or 256 bytes (3),
+  // the per-lane copy ring for rows of 512 bytes to 2 KB (4).
   const int64_t row_bytes = (int64_t)N * (int64_t)dtype_size(dt);
   const bool narrow = dt != SHIRO_F64 && (row_bytes == 128 || row_bytes == 256);
-  const int32_t pipes[] = {0, 3};
+  const bool ringable = dt != SHIRO_F64 && (row_bytes == 512 || row_bytes == 1024 ||
+                                            row_bytes == 2048);
+  const int32_t pipes[] = {5, 3, 4};
   for (int32_t gn : groups) {
     if (gn < avg / 2) continue;
     for (int32_t ch : chunks) {
@@ -732,6 +795,7 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
       for (int32_t w : warps) {
         for (int32_t pipe : pipes) {
           if (pipe == 3 && !narrow) continue;
+          if (pipe == 4 && !ringable) continue;
           shiro_opts o = start;
           o.group_nnz = gn;
           o.group_rows = 32;

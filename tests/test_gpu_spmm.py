@@ -155,8 +155,9 @@ def test_full_size_rmat20_sampled_rows(rmat20):
 @pytest.mark.parametrize("case", ["f32_n128", "f32_n256", "f32_n64", "f32_n32", "bf16_n128",
                                   "bf16_n256", "f64_n128", "local_diag", "accumulate", "hub"])
 def test_pipelines_bit_identical(case):
-    """Register gathers, per-lane async copies and TMA bulk copies sum every row in the same
-    order, so the three pipelines give bit-identical C (and each passes the oracle bound)."""
+    """Register gathers, per-lane async copies and TMA bulk copies in two stages, and the per-lane
+    copy ring sum every row in the same order, so all pipelines give bit-identical C (and each
+    passes the oracle bound)."""
     shiro = gu.lib()
     flags, vdt, dt, acc = 0, torch.float32, torch.float32, False
     A, N = synth.rmat(13, 12, 131), 128
@@ -185,9 +186,13 @@ def test_pipelines_bit_identical(case):
     else:
         Bd = torch.from_numpy(B).to(gu.dev()).to(dt)
     outs = []
-    for pipe in (0, 1, 2):
+    # (pipeline, stage_rows, persistent): automatic, forced register gathers, the two-stage
+    # copies, and the per-lane copy ring at each compiled depth (and persistent).
+    runs = [(5, 0, 0), (1, 0, 0), (2, 0, 0), (0, 0, 0), (4, 0, 0), (4, 4, 0), (4, 8, 0),
+            (4, 12, 0), (4, 16, 1), (4, 32, 0)]
+    for pipe, rows, pers in runs:
         opts = shiro.make_opts(pipeline=pipe, long_row_nnz=128, chunk_nnz=64, group_nnz=256,
-                               warps_per_cta=2)
+                               warps_per_cta=2, stage_rows=rows, persistent=pers)
         P = gu.plan_of(A, 4, 4, flags, opts=opts, vdt=vdt)
         Bp = P.pack(Bd)
         C = P.spmm(Bp, B=Bd)
@@ -198,6 +203,9 @@ def test_pipelines_bit_identical(case):
         outs.append(C.cpu())
     assert torch.equal(outs[0], outs[1]), "async pipeline differs from register gathers"
     assert torch.equal(outs[0], outs[2]), "bulk pipeline differs from register gathers"
+    for (pipe, rows, pers), out in zip(runs[3:], outs[3:]):
+        assert torch.equal(outs[0], out), \
+            f"pipeline {pipe} (rows {rows}, persistent {pers}) differs from register gathers"
     C = outs[0].numpy() / (2.0 if acc else 1.0)
     err = gu.scaled_err(C, oracle.spmm(A, B), oracle.abs_scale(A, B))
     assert err <= gu.TOL, err

@@ -96,8 +96,9 @@ typedef struct {
   int32_t persistent;    /* 1: grid = SMs x resident CTAs and warps stride over the items */
   int32_t pipeline;      /* How the gathered B rows reach the accumulators (every pipeline sums
                             a row's nonzeros in the same order, except 3):
-                            0: automatic -- 5 for rows below 1 KB, 4 for FP32/BF16 rows of
-                               1-2 KB (the faster of the two there, measured);
+                            0: automatic -- 6 for FP32/BF16 rows of 256 or 512 bytes (5 in
+                               persistent mode), 4 for FP32/BF16 rows of 1-2 KB, else 5 (the
+                               fastest measured for each row size);
                             1: staged through shared memory by per-lane asynchronous copies, two
                                stages per warp;
                             2: staged by one TMA bulk copy per row, two stages per warp (rows of
@@ -108,7 +109,12 @@ typedef struct {
                             4: a per-warp ring of row slots refilled by per-lane asynchronous
                                copies stage_rows rows ahead (FP32/BF16 rows of 256 bytes to 2 KB;
                                else 5);
-                            5: register gathers, 2-4 rows in flight per warp */
+                            5: register gathers, 2-4 rows in flight per warp, 64 registers;
+                            6: register gathers with a 48-register budget (FP32/BF16 rows of
+                               128-512 bytes; else 5): 2-warp CTAs, 40 warps per SM, the next
+                               batch's (index, value) pairs copied into shared memory
+                               asynchronously; warps_per_cta and persistent mode do not apply
+                               (persistent falls back to 5) */
   int32_t stage_rows;    /* pipeline 1: rows per stage, 8, 16 or 32 (0 = the largest that keeps a
                             stage within 16 KB); pipeline 4: ring depth, 16 or 32 for 256-byte
                             rows (0 = 16), 8, 12 or 16 for 512-byte rows (0 = 8), 4 or 8 for
@@ -327,8 +333,9 @@ shiro_status shiro_batch_plan_create(int32_t G, const shiro_csr* graphs, const s
  * C and scratch as for shiro_spmm; C is overwritten) and leaves the fastest one in the plan
  * (*best receives it).  Candidates vary the row-group size (from the average row length), the
  * chunk size of long rows (only when some row is longer), the CTA size and the pipeline: register
- * gathers, plus lane groups for rows of 128 or 256 bytes and the per-lane copy ring for FP32/BF16
- * rows of 512 bytes to 2 KB; the persistent mode stays as set.  Candidates whose scratch
+ * gathers, plus lane groups for rows of 128 or 256 bytes, the per-lane copy ring for FP32/BF16
+ * rows of 512 bytes to 2 KB and the 48-register gathers for FP32/BF16 rows of 128-512 bytes
+ * (outside persistent mode); the persistent mode stays as set.  Candidates whose scratch
  * does not fit scratch_bytes are skipped.  Synchronises `stream`. */
 shiro_status shiro_autotune(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
                             int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,

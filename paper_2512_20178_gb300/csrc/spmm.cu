@@ -332,6 +332,7 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Bas
 #include "spmm_bulk.cuh"
 #include "spmm_grouped.cuh"
 #include "spmm_ring.cuh"
+#include "spmm_lean.cuh"
 
 namespace shiro {
 
@@ -600,6 +601,24 @@ static shiro_status launch_lring(const shiro_plan_s* P, const SpmmParams<TV, TB>
   }
 }
 
+template <typename TV, typename TB, int VEC, int NCH>
+static shiro_status launch_lean(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                cudaStream_t s) {
+  constexpr int U = Occupancy<VEC, NCH, TB>::U;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm_lean<TV, TB, VEC, NCH, U, true>
+                    : k_spmm_lean<TV, TB, VEC, NCH, U, false>;
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.chunk_blocks = (q.n_chunk_items + 1) / 2;
+  const int64_t grid = q.chunk_blocks + (prm.n_items - q.n_chunk_items + 1) / 2;
+  if (grid <= 0) return SHIRO_OK;
+  if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+  kern<<<(unsigned)grid, 64, 0, s>>>(q);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
 template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
                                cudaStream_t s) {
@@ -612,6 +631,13 @@ static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& 
                   (ROW & (ROW - 1)) == 0) {
       if (P->opts.pipeline == 4 || (P->opts.pipeline == 0 && ROW >= 1024))
         return launch_lring<TV, TB, VEC, NCH>(P, prm, s);
+    }
+    // Lean register gathers (pipeline 6; 48 registers, 2-warp CTAs, no persistent mode): with
+    // pipeline 0 (automatic) rows of 256 or 512 bytes take them (measured faster there).
+    if constexpr (!std::is_same<TB, double>::value && NCH == 1 && ROW >= 128 && ROW <= 512) {
+      if (!P->opts.persistent &&
+          (P->opts.pipeline == 6 || (P->opts.pipeline == 0 && ROW >= 256)))
+        return launch_lean<TV, TB, VEC, NCH>(P, prm, s);
     }
     if (P->opts.pipeline == 2 && bulk_ok<TV, TB, VEC, NCH>(P, prm))
       return launch_bulk<TV, TB, VEC, NCH>(P, prm, s);
@@ -782,12 +808,15 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
   const int32_t chunks[] = {256, 512, 1024};
   const int32_t warps[] = {1, 2, 4};
   // Pipelines worth trying: register gathers (5), lane groups when rows are 128 or 256 bytes (3),
-  // the per-lane copy ring for rows of 512 bytes to 2 KB (4).
+  // the per-lane copy ring for rows of 512 bytes to 2 KB (4), lean register gathers for rows of
+  // 128 to 512 bytes (6, not in persistent mode).
   const int64_t row_bytes = (int64_t)N * (int64_t)dtype_size(dt);
   const bool narrow = dt != SHIRO_F64 && (row_bytes == 128 || row_bytes == 256);
   const bool ringable = dt != SHIRO_F64 && (row_bytes == 512 || row_bytes == 1024 ||
                                             row_bytes == 2048);
-  const int32_t pipes[] = {5, 3, 4};
+  const bool leanable = dt != SHIRO_F64 && !start.persistent &&
+                        (row_bytes == 128 || row_bytes == 256 || row_bytes == 512);
+  const int32_t pipes[] = {5, 3, 4, 6};
   for (int32_t gn : groups) {
     if (gn < avg / 2) continue;
     for (int32_t ch : chunks) {
@@ -796,6 +825,7 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
         for (int32_t pipe : pipes) {
           if (pipe == 3 && !narrow) continue;
           if (pipe == 4 && !ringable) continue;
+          if (pipe == 6 && (!leanable || w != 1)) continue;  // lean CTAs are always 2 warps
           shiro_opts o = start;
           o.group_nnz = gn;
           o.group_rows = 32;

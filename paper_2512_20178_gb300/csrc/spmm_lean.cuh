@@ -1,0 +1,171 @@
+// spmm_lean.cuh -- register gathers with a 48-register budget, so that 40 warps fit on an SM
+// (2-warp CTAs, 20 per SM) instead of 32: more rows in flight per SM for the same U per warp.
+//
+// What the 64-register loop keeps in registers and this one does not:
+//   * the (index, value) pairs of the next batch: copied straight into the other half of a
+//     double-buffered shared-memory batch by cp.async (4-byte copies, no register staging);
+//   * the values of the rows in flight: read again from shared memory at the FMA;
+//   * per-lane row state: one word, the row's end relative to the item's first nonzero, 0 for
+//     rows that end nowhere (empty rows and lanes past the item's rows).
+// Rows are summed in the same order as the other pipelines, so C is bit-identical to them.
+#pragma once
+
+#include "internal.cuh"
+#include "vec.cuh"
+
+namespace shiro {
+
+// 2-warp CTAs resident per SM (65,536 registers / (20 x 64 threads) -> 48 registers per thread).
+// Measured against 24 (40 registers) on R-MAT 2^20, 4x4 tiles: 48 registers is as fast or faster
+// for FP32 N = 128 and clearly faster for FP32 N = 64 and BF16 N = 128 / 256.
+constexpr int LEAN_MIN_BLOCKS = 20;
+
+// FP32 rows in float4 fragments (16 registers per U = 4 rows in flight) take one loop copy for
+// full and partial batches: the three copies spill there (112 bytes at 48 registers; FP32 N = 128
+// 0.680 ms against 0.623 ms with one copy).  Other rows take the three copies.
+template <typename TB, int VEC>
+struct LeanShape {
+  static constexpr bool ONE_COPY = std::is_same<TB, float>::value && VEC == 4;
+};
+
+template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL, bool FULL, bool ENDS>
+__device__ __forceinline__ void lean_batch(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
+                                           const Pair<TV>* sp, int n, int off, int32_t r0, int rel,
+                                           unsigned endmask,
+                                           typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
+  static_assert(32 % U == 0, "U must divide the 32-pair batch");
+#pragma unroll 1
+  for (int j = 0; j < (FULL ? 32 : n); j += U) {
+    typename RawFrag<TB, VEC>::T b[U][NCH][RawFrag<TB, VEC>::W];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (FULL || j + u < n) {
+        const int32_t idx = sp[j + u].idx;
+        // bs holds this lane's slice of row 0 (gather_raw adds only the chunk offsets).
+        const TB* row;
+        if (LOCAL && idx < 0)
+          row = bs.b + (uint64_t)(uint32_t)(-1 - idx) * bs.ldb;
+        else
+          row = bs.bp + (uint64_t)(uint32_t)idx * bs.ldp;
+        gather_raw<TV, TB, VEC, NCH, false>(p, row, b[u], lane);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (FULL || j + u < n) {
+        const TV a = sp[j + u].val;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) fma_raw<TB, VEC>(a, b[u][c], acc[c]);
+        if (ENDS && ((endmask >> (j + u)) & 1u)) {
+          const unsigned who = __ballot_sync(0xffffffffu, rel == off + j + u + 1);
+          flush_row<TV, TB, VEC, NCH, false>(p, r0 + __ffs(who) - 1, acc, lane);
+        }
+      }
+    }
+  }
+}
+
+// Nonzeros [base, base + total) of rows r0 .. (lane l: rel = end of row r0 + l relative to base
+// if that row is non-empty, else 0).  sp holds two batches of 32 pairs.
+template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
+__device__ __forceinline__ void lean_span(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
+                                          Pair<TV>* sp, int64_t base, int total, int32_t r0,
+                                          int rel, typename AccOf<TB>::T (&acc)[NCH][VEC],
+                                          int lane) {
+  if (total <= 0) return;
+  __syncwarp();
+  if (lane < total) {
+    Pair<TV> pr;
+    pr.idx = __ldcs(p.remap + base + lane);
+    pr.val = __ldcs(p.val + base + lane);
+    sp[lane] = pr;
+  }
+#pragma unroll 1
+  for (int off = 0; off < total; off += 32) {
+    Pair<TV>* cur = sp + ((off >> 5) & 1) * 32;
+    Pair<TV>* nxt = sp + (((off >> 5) + 1) & 1) * 32;
+    cp_async_wait<0>();
+    __syncwarp();
+    // The next batch's pairs land in the other half while this batch's gathers are in flight
+    // (that half held the batch before this one, which every lane has finished with).
+    if (off + 32 + lane < total) {
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(nxt + lane);
+      cp_async<4>(d, p.remap + base + off + 32 + lane);
+      cp_async<(int)sizeof(TV)>(d + (uint32_t)offsetof(Pair<TV>, val),
+                                p.val + base + off + 32 + lane);
+    }
+    cp_async_commit();
+    const int n = min(32, total - off);
+    const int q = rel - 1 - off;
+    const unsigned endmask = __reduce_or_sync(0xffffffffu, (q >= 0 && q < 32) ? (1u << q) : 0u);
+    if constexpr (LeanShape<TB, VEC>::ONE_COPY) {
+      lean_batch<TV, TB, VEC, NCH, U, LOCAL, false, true>(p, bs, cur, n, off, r0, rel, endmask,
+                                                          acc, lane);
+    } else {
+      // Full batches without a row end (all chunk batches, most batches of long rows) take a copy
+      // without per-nonzero tests; full batches with row ends a copy without bounds tests.
+      if (n == 32 && endmask == 0)
+        lean_batch<TV, TB, VEC, NCH, U, LOCAL, true, false>(p, bs, cur, n, off, r0, rel, endmask,
+                                                            acc, lane);
+      else if (n == 32)
+        lean_batch<TV, TB, VEC, NCH, U, LOCAL, true, true>(p, bs, cur, n, off, r0, rel, endmask,
+                                                           acc, lane);
+      else
+        lean_batch<TV, TB, VEC, NCH, U, LOCAL, false, true>(p, bs, cur, n, off, r0, rel, endmask,
+                                                            acc, lane);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// Blocks [0, chunk_blocks) run the chunks of long rows, the others the row groups; two warps per
+// block, one item per warp (no persistent mode).
+template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
+__global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS) k_spmm_lean(const SpmmParams<TV, TB> p) {
+  using TA = typename AccOf<TB>::T;
+  __shared__ Pair<TV> s_pairs[2][64];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  Pair<TV>* sp = s_pairs[warp];
+  Bases<TB> bs;
+  bs.bp = p.Bpack + lane * VEC;
+  bs.b = p.B + lane * VEC;
+  bs.ldp = (uint32_t)p.ldp;
+  bs.ldb = (uint32_t)p.ldb;
+  TA acc[NCH][VEC];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
+  if ((int64_t)blockIdx.x < p.chunk_blocks) {
+    const int64_t it = (int64_t)blockIdx.x * 2 + warp;
+    if (it >= p.n_chunk_items) return;
+    const Item item = p.items[it];
+    const int64_t row_end = __ldg(p.rowptr + item.row + 1);
+    const int total = (int)min((int64_t)p.chunk, row_end - item.e0);
+    lean_span<TV, TB, VEC, NCH, U, LOCAL>(p, bs, sp, item.e0, total, item.row, 0, acc, lane);
+    finish_chunk<TV, TB, VEC, NCH, false>(p, -item.tag - 1, acc, lane);
+  } else {
+    const int64_t it = p.n_chunk_items + ((int64_t)blockIdx.x - p.chunk_blocks) * 2 + warp;
+    if (it >= p.n_items) return;
+    const Item item = p.items[it];
+    const int32_t r0 = item.row, nr = item.tag;
+    const int64_t rp = lane < nr ? __ldg(p.rowptr + r0 + lane + 1) : 0;
+    int rel = (int)(rp - item.e0);
+    const int prev = __shfl_up_sync(0xffffffffu, rel, 1);
+    const bool nonempty = lane < nr && rel > (lane ? prev : 0);
+    const int total = __shfl_sync(0xffffffffu, rel, nr - 1);
+    if (!p.accumulate) {
+      unsigned empty = __ballot_sync(0xffffffffu, lane < nr && !nonempty);
+      while (empty) {
+        const int l = __ffs(empty) - 1;
+        empty &= empty - 1;
+        flush_row<TV, TB, VEC, NCH, false>(p, r0 + l, acc, lane);
+      }
+    }
+    rel = nonempty ? rel : 0;
+    lean_span<TV, TB, VEC, NCH, U, LOCAL>(p, bs, sp, item.e0, total, r0, rel, acc, lane);
+  }
+}
+
+}  // namespace shiro

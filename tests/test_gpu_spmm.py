@@ -155,9 +155,9 @@ def test_full_size_rmat20_sampled_rows(rmat20):
 @pytest.mark.parametrize("case", ["f32_n128", "f32_n256", "f32_n64", "f32_n32", "bf16_n128",
                                   "bf16_n256", "f64_n128", "local_diag", "accumulate", "hub"])
 def test_pipelines_bit_identical(case):
-    """Register gathers, per-lane async copies and TMA bulk copies in two stages, and the per-lane
-    copy ring sum every row in the same order, so all pipelines give bit-identical C (and each
-    passes the oracle bound)."""
+    """Register gathers (64- and 48-register forms), per-lane async copies and TMA bulk copies in
+    two stages, and the per-lane copy ring sum every row in the same order, so all pipelines give
+    bit-identical C (and each passes the oracle bound)."""
     shiro = gu.lib()
     flags, vdt, dt, acc = 0, torch.float32, torch.float32, False
     A, N = synth.rmat(13, 12, 131), 128
@@ -186,10 +186,11 @@ def test_pipelines_bit_identical(case):
     else:
         Bd = torch.from_numpy(B).to(gu.dev()).to(dt)
     outs = []
-    # (pipeline, stage_rows, persistent): automatic, forced register gathers, the two-stage
-    # copies, and the per-lane copy ring at each compiled depth (and persistent).
+    # (pipeline, stage_rows, persistent): forced register gathers, the two-stage copies, automatic,
+    # the per-lane copy ring at each compiled depth (and persistent), the 48-register gathers
+    # (and their persistent fallback).
     runs = [(5, 0, 0), (1, 0, 0), (2, 0, 0), (0, 0, 0), (4, 0, 0), (4, 4, 0), (4, 8, 0),
-            (4, 12, 0), (4, 16, 1), (4, 32, 0)]
+            (4, 12, 0), (4, 16, 1), (4, 32, 0), (6, 0, 0), (6, 0, 1)]
     for pipe, rows, pers in runs:
         opts = shiro.make_opts(pipeline=pipe, long_row_nnz=128, chunk_nnz=64, group_nnz=256,
                                warps_per_cta=2, stage_rows=rows, persistent=pers)

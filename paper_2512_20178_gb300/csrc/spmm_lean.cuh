@@ -21,8 +21,9 @@ namespace shiro {
 constexpr int LEAN_MIN_BLOCKS = 20;
 
 // FP32 rows in float4 fragments (16 registers per U = 4 rows in flight) take one loop copy for
-// full and partial batches: the three copies spill there (112 bytes at 48 registers; FP32 N = 128
-// 0.680 ms against 0.623 ms with one copy).  Other rows take the three copies.
+// full and partial batches: three copies spill there (112 bytes at 48 registers), and so does a
+// copy for full batches with row ends; one copy ran FP32 N = 128 in 0.561 ms against 0.680 (three
+// copies) and 0.635 (two).  Other rows take the three copies.
 template <typename TB, int VEC>
 struct LeanShape {
   static constexpr bool ONE_COPY = std::is_same<TB, float>::value && VEC == 4;
@@ -50,13 +51,27 @@ __device__ __forceinline__ void lean_batch(const SpmmParams<TV, TB>& p, const Ba
         gather_raw<TV, TB, VEC, NCH, false>(p, row, b[u], lane);
       }
     }
+    // One test per step for row ends among its U nonzeros (most steps have none): a step without
+    // one takes the FMAs alone (one copy at 48 registers: 0.617 -> 0.561 ms for FP32 N = 128).
+    const unsigned em = ENDS ? (endmask >> j) & ((1u << U) - 1u) : 0u;
+    if (em == 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (FULL || j + u < n) {
+          const TV a = sp[j + u].val;
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) fma_raw<TB, VEC>(a, b[u][c], acc[c]);
+        }
+      }
+      continue;
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (FULL || j + u < n) {
         const TV a = sp[j + u].val;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) fma_raw<TB, VEC>(a, b[u][c], acc[c]);
-        if (ENDS && ((endmask >> (j + u)) & 1u)) {
+        if (ENDS && ((em >> u) & 1u)) {
           const unsigned who = __ballot_sync(0xffffffffu, rel == off + j + u + 1);
           flush_row<TV, TB, VEC, NCH, false>(p, r0 + __ffs(who) - 1, acc, lane);
         }

@@ -114,7 +114,8 @@ typedef struct {
                                128-512 bytes; else 5): 2-warp CTAs, 40 warps per SM, the next
                                batch's (index, value) pairs copied into shared memory
                                asynchronously; warps_per_cta and persistent mode do not apply
-                               (persistent falls back to 5) */
+                               (persistent falls back to 5).
+                            shiro_sddmm reads 5 and 6 too (see there). */
   int32_t stage_rows;    /* pipeline 1: rows per stage, 8, 16 or 32 (0 = the largest that keeps a
                             stage within 16 KB); pipeline 4: ring depth, 16 or 32 for 256-byte
                             rows (0 = 16), 8, 12 or 16 for 512-byte rows (0 = 8), 4 or 8 for
@@ -302,7 +303,11 @@ shiro_status shiro_spmm_noalloc(shiro_plan_t plan, const void* Bpack, int64_t ld
 
 /* Gradient of C = A B with respect to A's stored values (a sampled dense-dense product on A's
  * pattern): dA[e] = sum_k dC[row(e), k] * Bpack[remap[e], k] (B[col[e], k] for local diagonal
- * tiles).  dC: device M x N of dt (F32/BF16 with F32 dA, or F64 with F64 dA). */
+ * tiles).  dC: device M x N of dt (F32/BF16 with F32 dA, or F64 with F64 dA).  The plan's
+ * schedule options pick the kernel: BF16 rows of 256 or 512 bytes reduce each dot product through
+ * a shared-memory tile (48 registers, 40 warps per SM) unless pipeline is 5 or persistent is set;
+ * other rows, and those, use a warp-shuffle reduction (FP32 rows take the tile with pipeline 6).
+ * Each kernel sums in a fixed order, so dA is deterministic for a given kernel. */
 shiro_status shiro_sddmm(shiro_plan_t plan, const void* dC, int64_t lddc, const void* Bpack,
                          int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
                          void* dA, void* stream);

@@ -169,3 +169,47 @@ def test_gcn_full_fp32_vs_oracle():
     sc = np.einsum("ij,ij->i", np.abs(G[rows_e]).astype(np.float64), np.abs(Hh[A.col[es]]).astype(np.float64))
     got = dA.cpu().numpy()[es]
     assert np.all(np.abs(got - ref) <= gu.TOL * sc), "dA (sampled) beyond tolerance"
+
+
+@pytest.mark.parametrize("case", ["f32_n128", "f32_n64", "bf16_n128", "bf16_n256", "hub",
+                                  "local_diag", "empty_rows", "ragged"])
+def test_sddmm_kernels(case):
+    """dA by both SDDMM kernels -- the 48-register one (shared-memory tile reduction: the default
+    for BF16 rows of 256/512 bytes, pipeline 6 for FP32) and the shuffle-reduction one (FP32
+    default, pipeline 5, persistent mode) -- within the oracle bound on the same inputs, including
+    hub rows cut into chunks, 1D local diagonal tiles read from B in place, empty rows and a ragged
+    last batch."""
+    shiro = gu.lib()
+    flags, dt, N = 0, torch.float32, 128
+    A = synth.rmat(13, 12, 140)
+    if case == "f32_n64":
+        N = 64
+    elif case.startswith("bf16"):
+        dt = torch.bfloat16
+        N = 256 if case.endswith("256") else 128
+    elif case == "hub":
+        A = synth.hub_matrix(300, 1 << 15, 7, 20000, 3, 141)
+    elif case == "local_diag":
+        flags = shiro.SHIRO_PLAN_LOCAL_DIAG
+    elif case == "empty_rows":
+        A = synth.random_small(900, 700, 0.02, 142, empty_rows=300)
+    elif case == "ragged":
+        A = synth.random_small(333, 517, 0.037, 143)
+    B = synth.dense_normal(A.K, N, 144)
+    G = synth.dense_normal(A.M, N, 145)
+    if dt == torch.bfloat16:
+        B = synth.bf16_bits_to_f32(synth.to_bf16_bits(B)).reshape(B.shape)
+        G = synth.bf16_bits_to_f32(synth.to_bf16_bits(G)).reshape(G.shape)
+    d = gu.dev()
+    Bd = torch.from_numpy(B).to(d).to(dt)
+    Gd = torch.from_numpy(G).to(d).to(dt)
+    ref = oracle.sddmm(A, G, B)
+    scale = oracle.sddmm(A, np.abs(G), np.abs(B))
+    for pipe, pers in [(0, 0), (5, 0), (6, 0), (0, 1)]:
+        opts = shiro.make_opts(pipeline=pipe, persistent=pers, long_row_nnz=128, chunk_nnz=64)
+        P = gu.plan_of(A, 4, 4, flags, opts=opts)
+        Bp = P.pack(Bd)
+        dA = P.sddmm(Gd, Bp, B=Bd)
+        torch.cuda.synchronize()
+        err = gu.scaled_err(dA.cpu().numpy(), ref, scale)
+        assert err <= gu.TOL, f"pipeline {pipe} persistent {pers}: dA scaled error {err}"

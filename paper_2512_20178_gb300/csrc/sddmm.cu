@@ -2,9 +2,9 @@
 // (a sampled dense-dense product on A's pattern, reading B through the packed rows), and the
 // backward entry point that adds dB = A^T dC through the transposed plan.
 //
-// One warp per work item (the SpMM schedule).  BF16 rows of 256 or 512 bytes take the 48-register
-// kernel of sddmm_lean.cuh (partials reduced through a shared-memory tile; FP32 rows too with
-// pipeline 6).  The kernel here takes the other shapes and persistent mode: a batch of up to 32
+// One warp per work item (the SpMM schedule).  BF16 rows of 256 or 512 bytes and FP32 rows of 512
+// bytes take the 48-register kernels of sddmm_lean.cuh.  The kernel here takes the other shapes,
+// persistent mode and pipeline 5: a batch of up to 32
 // nonzeros is taken as four sub-batches of 8, every lane forms its slice of the 8 dot products, a
 // butterfly reduction (4+2+1 shuffles, then 2) completes them, and one more shuffle hands nonzero
 // j of the batch to lane j, which writes dA coalesced once per batch.
@@ -223,20 +223,26 @@ namespace shiro {
 template <typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& prm,
                                  cudaStream_t s) {
-  // BF16 rows of 256 or 512 bytes take the 48-register kernel outside persistent mode (pipeline 5
-  // keeps the shuffle-reduction kernel); FP32 rows only with pipeline 6.  Measured on R-MAT 2^20,
-  // 4x4 tiles (ms, shuffle-reduction -> 48-register): BF16 N = 256 1.82 -> 1.20, BF16 N = 128
-  // 0.92 -> 0.88, FP32 N = 128 0.93 -> 1.00, FP32 N = 64 0.78 -> 0.82 (the shared-memory tile
-  // competes with the gathers for L1 bandwidth there).
+  // 48-register kernels outside persistent mode and pipeline 5: BF16 rows of 256 or 512 bytes
+  // with the shared-memory tile reduction, FP32 rows of 512 bytes (N = 128) with the 4-wide
+  // shuffle butterfly; pipeline 6 takes the tile for FP32 rows of 256/512 bytes too.  Measured on
+  // R-MAT 2^20, 4x4 tiles (ms; 64-register shuffle kernel -> tile / 4-wide butterfly):
+  // BF16 N = 256 1.82 -> 1.20 / 1.20, BF16 N = 128 0.92 -> 0.88 / 0.88,
+  // FP32 N = 128 0.93 -> 1.00 / 0.887, FP32 N = 64 0.78 -> 0.82 / 0.81 (the tile competes with
+  // the gathers for L1 bandwidth; FP32 N = 64 keeps the 64-register kernel).
   if constexpr (!MASKED && NCH == 1 && !std::is_same<TB, double>::value &&
                 VEC * sizeof(TB) >= 8) {
-    const bool want = std::is_same<TB, __nv_bfloat16>::value ? P->opts.pipeline != 5
-                                                             : P->opts.pipeline == 6;
-    if (!prm.persistent && want) {
+    constexpr bool BF = std::is_same<TB, __nv_bfloat16>::value;
+    const bool tile = BF || P->opts.pipeline == 6;
+    const bool shfl = !BF && VEC == 4 && P->opts.pipeline != 6;  // FP32 N = 128 rows
+    if (!prm.persistent && P->opts.pipeline != 5 && (tile || shfl)) {
       const int64_t grid = (prm.n_items + 1) / 2;
       if (grid <= 0) return SHIRO_OK;
       if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
-      k_sddmm_lean<TB, VEC><<<(unsigned)grid, 64, 0, s>>>(prm);
+      if (tile)
+        k_sddmm_lean<TB, VEC, true><<<(unsigned)grid, 64, 0, s>>>(prm);
+      else if constexpr (!BF && VEC == 4)
+        k_sddmm_lean<TB, VEC, false><<<(unsigned)grid, 64, 0, s>>>(prm);
       SHIRO_CUDA(cudaGetLastError());
       return SHIRO_OK;
     }

@@ -1,5 +1,6 @@
 // sddmm_lean.cuh -- dA[e] = <dC[row e], B[col e]> with a 48-register budget, so that 40 warps fit
-// on an SM (2-warp CTAs, 20 per SM) instead of 32.
+// on an SM (2-warp CTAs, 20 per SM) instead of 32.  Two ways to finish the dot products: a 4-wide
+// shuffle butterfly per step of 4 nonzeros (four partial registers), or a shared-memory tile:
 //
 // Per batch of 32 nonzeros every lane forms its slice of each dot product (VEC products of its
 // dC slice and the gathered B slice) and stores it into a 32 x 32 shared-memory tile, row = the
@@ -52,10 +53,33 @@ struct SdLeanShape {
   static constexpr int U = (std::is_same<TB, __nv_bfloat16>::value && VEC == 8) ? 2 : 4;
 };
 
-template <typename TB, int VEC>
+// Dot products of 4 nonzeros, lane slices in part[0..3], summed over the warp: a butterfly over
+// lane bits 4, 3 (2 + 1 shuffles) leaves nonzero (lane >> 3) & 3 in every lane, three exchanges
+// over bits 2, 1, 0 complete its sum.  Four partials per lane.
+__device__ __forceinline__ float reduce4(float (&part)[4], int lane) {
+#pragma unroll
+  for (int off = 16, half = 2; off >= 8; off >>= 1, half >>= 1) {
+    const bool upper = lane & off;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float send = upper ? part[k] : part[k + half];
+      const float keep = upper ? part[k + half] : part[k];
+      part[k] = keep + __shfl_xor_sync(FULLM, send, off);
+    }
+  }
+  float r = part[0];
+  r += __shfl_xor_sync(FULLM, r, 4);
+  r += __shfl_xor_sync(FULLM, r, 2);
+  r += __shfl_xor_sync(FULLM, r, 1);
+  return r;
+}
+
+// TILE: partials through the shared-memory tile (sred); else a 4-wide shuffle butterfly per
+// step of 4 nonzeros (sred unused).
+template <typename TB, int VEC, bool TILE>
 __device__ __forceinline__ void sddmm_lean_item(const SddmmParams<TB>& p, int32_t* sidx,
                                                 float* sred, const Item& item, int lane) {
-  constexpr int U = SdLeanShape<TB, VEC>::U;
+  constexpr int U = TILE ? SdLeanShape<TB, VEC>::U : 4;
   const bool chunk = item.tag <= 0;
   const int32_t r0 = item.row;
   const int nr = chunk ? 1 : item.tag;
@@ -94,6 +118,7 @@ __device__ __forceinline__ void sddmm_lean_item(const SddmmParams<TB>& p, int32_
     const int n = min(32, total - off);
     const int q = rel - 1 - off;
     const unsigned endmask = __reduce_or_sync(FULLM, (q >= 0 && q < 32) ? (1u << q) : 0u);
+    float out = 0.f;
 #pragma unroll 1
     for (int j = 0; j < n; j += U) {
       typename RawFrag<TB, VEC>::T b[U][RawFrag<TB, VEC>::W];
@@ -107,11 +132,16 @@ __device__ __forceinline__ void sddmm_lean_item(const SddmmParams<TB>& p, int32_
         }
       }
       const unsigned em = (endmask >> j) & ((1u << U) - 1u);
+      float part[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
+        part[u] = 0.f;
         if (j + u < n) {
           const int t = j + u;
-          sred[t * 32 + (lane ^ t)] = dot_raw<TB, VEC>(g, b[u], 0.f);
+          if constexpr (TILE)
+            sred[t * 32 + (lane ^ t)] = dot_raw<TB, VEC>(g, b[u], 0.f);
+          else
+            part[u] = dot_raw<TB, VEC>(g, b[u], 0.f);
           if ((em >> u) & 1u) {
             // The stream leaves row r0 + cur here: move to the prefetched next row.
             cur = nxt;
@@ -125,6 +155,16 @@ __device__ __forceinline__ void sddmm_lean_item(const SddmmParams<TB>& p, int32_
           }
         }
       }
+      if constexpr (!TILE) {
+        // Lane t of the batch keeps nonzero t's sum (held by lanes with (lane >> 3) & 3 == t & 3).
+        const float r = reduce4(reinterpret_cast<float(&)[4]>(part), lane);
+        const float v = __shfl_sync(FULLM, r, (lane & 3) << 3);
+        if ((lane >> 2) == (j >> 2)) out = v;
+      }
+    }
+    if constexpr (!TILE) {
+      if (lane < n) p.dA[item.e0 + off + lane] = out;
+      continue;
     }
     __syncwarp();
     if (lane < n) {
@@ -139,16 +179,16 @@ __device__ __forceinline__ void sddmm_lean_item(const SddmmParams<TB>& p, int32_
   sd_wait_all();
 }
 
-template <typename TB, int VEC>
+template <typename TB, int VEC, bool TILE>
 __global__ void __launch_bounds__(64, SD_LEAN_MIN_BLOCKS) k_sddmm_lean(const SddmmParams<TB> p) {
   __shared__ __align__(16) int32_t s_idx[2][64];
-  __shared__ __align__(16) float s_red[2][32 * 32];
+  __shared__ __align__(16) float s_red[TILE ? 2 : 1][TILE ? 32 * 32 : 1];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t it = (int64_t)blockIdx.x * 2 + warp;
   if (it >= p.n_items) return;
   const Item item = p.items[it];
-  sddmm_lean_item<TB, VEC>(p, s_idx[warp], s_red[warp], item, lane);
+  sddmm_lean_item<TB, VEC, TILE>(p, s_idx[warp], TILE ? s_red[warp] : nullptr, item, lane);
 }
 
 }  // namespace shiro

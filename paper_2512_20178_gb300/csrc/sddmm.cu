@@ -313,6 +313,9 @@ shiro_status launch_sddmm(const shiro_plan_s* P, const void* dC, int64_t lddc, c
                           int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
                           void* dA, cudaStream_t s) {
   if (N < 0 || lddc < N || ldp < N) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "bad N or leading dimension");
+  // The gathers multiply a 32-bit row index by a 32-bit row stride.
+  if (ldp > (int64_t)UINT32_MAX || ldb > (int64_t)UINT32_MAX)
+    SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "leading dimensions of B / Bpack above 2^32 - 1 elements");
   if (P->nnz == 0) return SHIRO_OK;
   if (!dA || !dC) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null dA or dC");
   if (!Bpack && P->packed_rows > 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null Bpack");

@@ -752,6 +752,9 @@ shiro_status launch_spmm(const shiro_plan_s* P, const void* Bpack, int64_t ldp, 
                          int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
                          uint32_t flags, void* scratch, size_t scratch_bytes, cudaStream_t s) {
   if (N < 0 || ldp < N || ldc < N) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "bad N or leading dimension");
+  // The gathers multiply a 32-bit row index by a 32-bit row stride.
+  if (ldp > (int64_t)UINT32_MAX || ldb > (int64_t)UINT32_MAX)
+    SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "leading dimensions of B / Bpack above 2^32 - 1 elements");
   if (!C && P->M > 0 && N > 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null C");
   if (!Bpack && P->packed_rows > 0 && N > 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null Bpack");
   if ((P->flags & SHIRO_PLAN_LOCAL_DIAG) && (!B || ldb < N))

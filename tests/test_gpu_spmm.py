@@ -118,6 +118,26 @@ def test_scratch_too_small_rejected():
     assert ei.value.status == 3
 
 
+def test_huge_leading_dimension_rejected():
+    """A B / Bpack stride of 2^32 elements or more is refused on the host (the gathers form row
+    addresses from a 32-bit index times a 32-bit stride); nothing is launched."""
+    shiro = gu.lib()
+    A = synth.rmat(10, 4, 22)
+    P = gu.plan_of(A, 2, 2)
+    Bd = torch.from_numpy(synth.dense_normal(A.K, 32, 2)).to(gu.dev())
+    Bp = P.pack(Bd)
+    C = torch.empty((A.M, 32), dtype=torch.float32, device=gu.dev())
+    f32 = shiro.dtype_code(torch.float32)
+    with pytest.raises(shiro.ShiroError) as ei:
+        shiro.shiro_spmm(P.handle, Bp.data_ptr(), 1 << 32, None, 0, 32, f32, C.data_ptr(), 32, 0,
+                         None, 0, None)
+    assert ei.value.status == 4
+    with pytest.raises(shiro.ShiroError) as ei:
+        shiro.shiro_sddmm(P.handle, C.data_ptr(), 32, Bp.data_ptr(), 1 << 32, None, 0, 32, f32,
+                          C.data_ptr(), None)
+    assert ei.value.status == 4
+
+
 def test_autotune_keeps_result():
     A = synth.rmat(14, 16, 51)
     B = synth.dense_normal(A.K, 128, 52)

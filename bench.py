@@ -45,7 +45,7 @@ KERNEL_SOURCES = ["paper_2512_20178_gb300/csrc/spmm.cu", "paper_2512_20178_gb300
 def spmm_kernel(N, sz):
     """The SpMM kernel the automatic pipeline picks for N columns of sz-byte elements."""
     row = N * sz
-    if row in (256, 512):
+    if row in (128, 256, 512):
         return "k_spmm_lean"
     if row in (1024, 2048):
         return "k_spmm_lring"

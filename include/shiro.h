@@ -96,7 +96,7 @@ typedef struct {
   int32_t persistent;    /* 1: grid = SMs x resident CTAs and warps stride over the items */
   int32_t pipeline;      /* How the gathered B rows reach the accumulators (every pipeline sums
                             a row's nonzeros in the same order, except 3):
-                            0: automatic -- 6 for FP32/BF16 rows of 256 or 512 bytes (5 in
+                            0: automatic -- 6 for FP32/BF16 rows of 128 to 512 bytes (5 in
                                persistent mode), 4 for FP32/BF16 rows of 1-2 KB, else 5 (the
                                fastest measured for each row size);
                             1: staged through shared memory by per-lane asynchronous copies, two

@@ -633,10 +633,9 @@ static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& 
         return launch_lring<TV, TB, VEC, NCH>(P, prm, s);
     }
     // Lean register gathers (pipeline 6; 48 registers, 2-warp CTAs, no persistent mode): with
-    // pipeline 0 (automatic) rows of 256 or 512 bytes take them (measured faster there).
+    // pipeline 0 (automatic) rows of 128 to 512 bytes take them (measured faster there).
     if constexpr (!std::is_same<TB, double>::value && NCH == 1 && ROW >= 128 && ROW <= 512) {
-      if (!P->opts.persistent &&
-          (P->opts.pipeline == 6 || (P->opts.pipeline == 0 && ROW >= 256)))
+      if (!P->opts.persistent && (P->opts.pipeline == 6 || P->opts.pipeline == 0))
         return launch_lean<TV, TB, VEC, NCH>(P, prm, s);
     }
     if (P->opts.pipeline == 2 && bulk_ok<TV, TB, VEC, NCH>(P, prm))

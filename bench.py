@@ -68,6 +68,14 @@ def parse():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"],
                     help="storage of B (and of the packed rows); accumulation is FP32 either way")
+    ap.add_argument("--er", action="store_true",
+                    help="time the small 1D case instead: Erdos-Renyi 4096 x 4096, avg degree 8, "
+                         "values U(-1, 1), B 4096 x 32, P = 4 row blocks with local diagonal tiles "
+                         "(L2-resident and launch-bound: reported, not roofline-judged)")
+    ap.add_argument("--gcn", action="store_true",
+                    help="time the GCN layer instead: Y = A_hat (X W), A_hat the symmetric-normalised "
+                         "R-MAT 2^scale graph with self loops, X n x 256, W 256 x N, fwd + bwd "
+                         "through the autograd wrapper")
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched form instead: this many R-MAT graphs, n ~ U{100..20000}, "
                          "degree log-uniform [4, 40], B n x N in BF16, one CUDA-graph replay per step")
@@ -576,10 +584,128 @@ def run_batch(args):
         "gflops": 2.0 * nnz * N / (ms * 1e-3) / 1e9, "gpu_launches": 2 * args.steps}))
 
 
+def run_er(args):
+    """The small 1D configuration: ER G(4096, 8/4096), N = 32, P = 4 row blocks whose diagonal
+    tiles read B in place (LOCAL_DIAG) and whose off-diagonal tiles are packed."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2512_20178_gb300 import shiro, synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, N, P_ = 4096, 32, 4
+    A = synth.er(n, 8, 1)
+    Bd = torch.from_numpy(synth.dense_normal(n, N, 1)).to(dev)
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    col = torch.from_numpy(A.col).to(dev)
+    val = torch.from_numpy(A.val).to(dev)
+    P = shiro.Plan.create(rp, col, val, A.M, A.K, P_, P_, flags=shiro.SHIRO_PLAN_LOCAL_DIAG)
+    R = P.info.packed_rows
+    Bp = torch.empty((max(R, 1), N), dtype=torch.float32, device=dev)
+    C = torch.empty((A.M, N), dtype=torch.float32, device=dev)
+    scratch = P.new_scratch(N, torch.float32)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        P.pack(Bd, out=Bp)
+        P.spmm(Bp, B=Bd, out=C, scratch=scratch)
+    K = max(args.steps, 100)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(K):
+        P.pack(Bd, out=Bp)
+        P.spmm(Bp, B=Bd, out=C, scratch=scratch)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    # Bytes: SpMM reads the packed rows of off-diagonal tiles and, in place, the B rows named by
+    # the diagonal tiles' Cols.
+    ncols = P.tile_stats()["tile_ncols"].numpy()
+    diag_cols = int(sum(ncols[p * P_ + p] for p in range(P_)))
+    sp, pk = step_bytes(A.M, A.nnz, R + diag_cols, N, 4)
+    pk = 2 * R * N * 4 + R * 4
+    print(json.dumps({
+        "metric": METRIC, "value": (sp + pk) / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+        "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "f32",
+        "data": "synthetic (seeded Erdos-Renyi)",
+        "config": {"workload": "er4096_deg8_N32_1d_p4_local_diag", "M": A.M, "nnz": A.nnz,
+                   "N": N, "packed_rows_offdiag": R, "diag_cols": diag_cols,
+                   "l2": "L2-resident (launch-bound)"},
+        "note": "two launches per step of a few microseconds each: reported, not roofline-judged",
+        "gpu_launches": 2 * K}))
+
+
+def run_gcn(args):
+    """GCN layer Y = A_hat (X W) through the public autograd wrapper: the dense product X W is
+    torch's (glue, timed on its own), A_hat times it is the library's pack + SpMM, and the backward
+    gives dX and dW through torch and dH (A_hat^T dY: pack + SpMM on the transposed plan) and the
+    gradient of A_hat's values (SDDMM) through the library.  Loss <G, Y> with a fixed G."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2512_20178_gb300 import autograd, synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seed = 4
+    A = synth.gcn_normalized(args.scale, args.deg, seed)
+    F, N = 256, args.N
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    col = torch.from_numpy(A.col).to(dev)
+    val = torch.from_numpy(A.val).to(dev).requires_grad_(True)
+    t0 = time.perf_counter()
+    S = autograd.SparseMatrix(rp, col, val, A.M, A.K, args.tiles, args.tiles)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    X = torch.from_numpy(synth.dense_normal(A.M, F, seed, std=0.02)).to(dev).requires_grad_(True)
+    W = torch.from_numpy(synth.dense_normal(F, N, seed + 1, std=0.02)).to(dev).requires_grad_(True)
+    G = torch.from_numpy(synth.dense_normal(A.M, N, seed + 2)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        return autograd.spmm(S, torch.matmul(X, W))
+
+    def fwd_bwd():
+        X.grad = W.grad = val.grad = None
+        fwd().backward(G)
+
+    def timed(fn, k):
+        for _ in range(args.warmup):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    with torch.no_grad():
+        H = torch.matmul(X, W)
+        glue_ms = timed(lambda: torch.matmul(X, W, out=H), args.steps)
+        sparse_fwd_ms = timed(lambda: autograd.spmm(S, H), args.steps)
+    fwd_ms = timed(fwd, args.steps)
+    ms = timed(fwd_bwd, args.steps)
+    print(json.dumps({
+        "metric": "GCN layer fwd+bwd ms", "value": ms, "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "f32",
+        "data": "synthetic (seeded R-MAT, symmetrised, self loops, 1/sqrt(d_i d_j))",
+        "config": {"workload": f"gcn_rmat{args.scale}_deg{args.deg}_F{F}_N{N}_{args.tiles}x{args.tiles}",
+                   "M": A.M, "nnz": A.nnz, "F": F, "N": N, "plan_ms": plan_ms,
+                   "packed_rows": S.plan.info.packed_rows,
+                   "packed_rows_transpose": S.planT.info.packed_rows},
+        "fwd_ms": fwd_ms, "dense_xw_ms": glue_ms, "sparse_fwd_ms": sparse_fwd_ms,
+        "sparse_fwd_gflops": 2.0 * A.nnz * N / (sparse_fwd_ms * 1e-3) / 1e9}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.gcn:
+        run_gcn(args)
+    elif args.er:
+        run_er(args)
     elif args.batch:
         run_batch(args)
     else:

@@ -46,7 +46,7 @@ def spmm_kernel(N, sz):
     """The SpMM kernel the automatic pipeline picks for N columns of sz-byte elements."""
     row = N * sz
     if row in (128, 256, 512):
-        return "k_spmm_lean"
+        return "k_spmm_lean" if (sz == 2 and row == 256) else "k_spmm_lean_dyn"
     if row in (1024, 2048):
         return "k_spmm_lring"
     return "k_spmm"

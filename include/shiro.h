@@ -93,12 +93,14 @@ typedef struct {
   int32_t group_nnz;
   int32_t group_rows;
   int32_t warps_per_cta; /* 1..8 */
-  int32_t persistent;    /* 1: grid = SMs x resident CTAs and warps stride over the items */
+  int32_t persistent;    /* 1: grid = SMs x resident CTAs; the warps of pipeline 6 take items
+                            from a counter, those of the other pipelines stride over them */
   int32_t pipeline;      /* How the gathered B rows reach the accumulators (every pipeline sums
                             a row's nonzeros in the same order, except 3):
-                            0: automatic -- 6 for FP32/BF16 rows of 128 to 512 bytes (5 in
-                               persistent mode), 4 for FP32/BF16 rows of 1-2 KB, else 5 (the
-                               fastest measured for each row size);
+                            0: automatic -- 6 for FP32/BF16 rows of 128 to 512 bytes (in its
+                               counter form except for BF16 rows of 256 bytes; 5 in persistent
+                               mode), 4 for FP32/BF16 rows of 1-2 KB, else 5 (the fastest
+                               measured for each row size);
                             1: staged through shared memory by per-lane asynchronous copies, two
                                stages per warp;
                             2: staged by one TMA bulk copy per row, two stages per warp (rows of
@@ -113,8 +115,8 @@ typedef struct {
                             6: register gathers with a 48-register budget (FP32/BF16 rows of
                                128-512 bytes; else 5): 2-warp CTAs, 40 warps per SM, the next
                                batch's (index, value) pairs copied into shared memory
-                               asynchronously; warps_per_cta and persistent mode do not apply
-                               (persistent falls back to 5).
+                               asynchronously; warps_per_cta does not apply; one item per warp,
+                               or with persistent set, items taken from a counter in the plan.
                             shiro_sddmm reads 5 and 6 too (see there). */
   int32_t stage_rows;    /* pipeline 1: rows per stage, 8, 16 or 32 (0 = the largest that keeps a
                             stage within 16 KB); pipeline 4: ring depth, 16 or 32 for 256-byte
@@ -276,7 +278,9 @@ shiro_status shiro_spmm_scratch(shiro_plan_t plan, int32_t N, shiro_dtype dt, si
  * stored order, i.e. ascending column blocks for column-sorted rows.
  * Types: values F32 with dt F32 or BF16 (C is F32, accumulation in FP32), or values F64 with dt
  * F64 (C is F64).  B may be NULL unless the plan has LOCAL_DIAG.  scratch: device, at least
- * shiro_spmm_scratch bytes (may be NULL when that is 0); its contents need no initialisation. */
+ * shiro_spmm_scratch bytes (may be NULL when that is 0); its contents need no initialisation.
+ * A plan holds the arrival counters of split rows and a work counter used by these calls, so
+ * compute calls on one plan must not overlap on the GPU (serialise them on one stream). */
 shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
                         int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
                         uint32_t flags, void* scratch, size_t scratch_bytes, void* stream);

@@ -49,6 +49,7 @@ struct SpmmParams {
   int32_t persistent;
   int* status;
   int32_t pf_bytes;  // bytes of a row to prefetch into L2 ahead of its gather (0: off)
+  int32_t* work;     // item counter of the dynamically scheduled kernel (zeroed before launch)
 };
 
 // (index, value) of one nonzero as staged in shared memory; two FP32 entries fill 16 bytes.
@@ -608,11 +609,25 @@ static shiro_status launch_lean(const shiro_plan_s* P, const SpmmParams<TV, TB>&
   const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
   auto kern = local ? k_spmm_lean<TV, TB, VEC, NCH, U, true>
                     : k_spmm_lean<TV, TB, VEC, NCH, U, false>;
+  // Persistent form: explicitly requested, or chosen per row shape by the automatic pipeline.
+  const bool dyn = prm.persistent || (P->opts.pipeline == 0 && LeanShape<TB, VEC>::DYN);
+  if (dyn)
+    kern = local ? k_spmm_lean_dyn<TV, TB, VEC, NCH, U, true>
+                 : k_spmm_lean_dyn<TV, TB, VEC, NCH, U, false>;
   SpmmParams<TV, TB> q = prm;
   q.n_chunk_items = P->n_slots;
   q.chunk_blocks = (q.n_chunk_items + 1) / 2;
-  const int64_t grid = q.chunk_blocks + (prm.n_items - q.n_chunk_items + 1) / 2;
+  int64_t grid = q.chunk_blocks + (prm.n_items - q.n_chunk_items + 1) / 2;
   if (grid <= 0) return SHIRO_OK;
+  if (dyn) {
+    // Persistent: SMs x resident CTAs, every warp takes the next item from a counter.
+    if (prm.n_items > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+    int per_sm = 0;
+    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, 0));
+    grid = std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * P->sm_count);
+    q.work = P->d_status + 2;
+    SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));
+  }
   if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
   kern<<<(unsigned)grid, 64, 0, s>>>(q);
   SHIRO_CUDA(cudaGetLastError());
@@ -632,10 +647,11 @@ static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& 
       if (P->opts.pipeline == 4 || (P->opts.pipeline == 0 && ROW >= 1024))
         return launch_lring<TV, TB, VEC, NCH>(P, prm, s);
     }
-    // Lean register gathers (pipeline 6; 48 registers, 2-warp CTAs, no persistent mode): with
-    // pipeline 0 (automatic) rows of 128 to 512 bytes take them (measured faster there).
+    // Lean register gathers (pipeline 6; 48 registers, 2-warp CTAs; persistent mode takes items
+    // from a counter): with pipeline 0 (automatic) rows of 128 to 512 bytes take them outside
+    // persistent mode (measured faster there), in the counter form for most row shapes.
     if constexpr (!std::is_same<TB, double>::value && NCH == 1 && ROW >= 128 && ROW <= 512) {
-      if (!P->opts.persistent && (P->opts.pipeline == 6 || P->opts.pipeline == 0))
+      if (P->opts.pipeline == 6 || (P->opts.pipeline == 0 && !P->opts.persistent))
         return launch_lean<TV, TB, VEC, NCH>(P, prm, s);
     }
     if (P->opts.pipeline == 2 && bulk_ok<TV, TB, VEC, NCH>(P, prm))

@@ -27,6 +27,11 @@ constexpr int LEAN_MIN_BLOCKS = 20;
 template <typename TB, int VEC>
 struct LeanShape {
   static constexpr bool ONE_COPY = std::is_same<TB, float>::value && VEC == 4;
+  // The automatic pipeline runs the persistent form (items from a counter) for every row shape
+  // but BF16 rows of 256 bytes, measured slower with it (R-MAT 2^20, 4x4 tiles, ms, one item per
+  // warp -> counter): FP32 N = 128 0.567 -> 0.554, N = 64 0.391 -> 0.371, N = 32 0.355 -> 0.331,
+  // BF16 N = 256 0.815 -> 0.769 (R-MAT 2^22: 6.52 -> 6.16), BF16 N = 128 0.453 -> 0.474.
+  static constexpr bool DYN = !(std::is_same<TB, __nv_bfloat16>::value && VEC == 4);
 };
 
 template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL, bool FULL, bool ENDS>
@@ -180,6 +185,62 @@ __global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS) k_spmm_lean(const SpmmPar
     }
     rel = nonempty ? rel : 0;
     lean_span<TV, TB, VEC, NCH, U, LOCAL>(p, bs, sp, item.e0, total, r0, rel, acc, lane);
+  }
+}
+
+// Persistent form (SMs x resident blocks of two warps): every warp takes the next item from a
+// counter (zeroed before the launch) until none is left, chunks of long rows first, so a warp
+// whose item ends early does not wait for its block's other warp.  Kept apart from k_spmm_lean:
+// a loop around both item paths costs that kernel registers.
+template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
+__global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS)
+    k_spmm_lean_dyn(const SpmmParams<TV, TB> p) {
+  using TA = typename AccOf<TB>::T;
+  __shared__ Pair<TV> s_pairs[2][64];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  Pair<TV>* sp = s_pairs[warp];
+  Bases<TB> bs;
+  bs.bp = p.Bpack + lane * VEC;
+  bs.b = p.B + lane * VEC;
+  bs.ldp = (uint32_t)p.ldp;
+  bs.ldb = (uint32_t)p.ldb;
+  const int n_items = (int)p.n_items, n_chunks = (int)p.n_chunk_items;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(p.work, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const Item item = p.items[it];
+    TA acc[NCH][VEC];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
+    int32_t r0 = item.row;
+    int rel = 0, total;
+    if (it < n_chunks) {
+      total = (int)min((int64_t)p.chunk, __ldg(p.rowptr + item.row + 1) - item.e0);
+    } else {
+      const int nr = item.tag;
+      const int64_t rp = lane < nr ? __ldg(p.rowptr + r0 + lane + 1) : 0;
+      rel = (int)(rp - item.e0);
+      const int prev = __shfl_up_sync(0xffffffffu, rel, 1);
+      const bool nonempty = lane < nr && rel > (lane ? prev : 0);
+      total = __shfl_sync(0xffffffffu, rel, nr - 1);
+      if (!p.accumulate) {
+        unsigned empty = __ballot_sync(0xffffffffu, lane < nr && !nonempty);
+        while (empty) {
+          const int l = __ffs(empty) - 1;
+          empty &= empty - 1;
+          flush_row<TV, TB, VEC, NCH, false>(p, r0 + l, acc, lane);
+        }
+      }
+      rel = nonempty ? rel : 0;
+    }
+    // One span call for both kinds of item (a chunk has no row end: rel = 0 in every lane).
+    lean_span<TV, TB, VEC, NCH, U, LOCAL>(p, bs, sp, item.e0, total, r0, rel, acc, lane);
+    if (it < n_chunks) finish_chunk<TV, TB, VEC, NCH, false>(p, -item.tag - 1, acc, lane);
   }
 }
 

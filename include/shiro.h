@@ -309,11 +309,11 @@ shiro_status shiro_spmm_noalloc(shiro_plan_t plan, const void* Bpack, int64_t ld
  * pattern): dA[e] = sum_k dC[row(e), k] * Bpack[remap[e], k] (B[col[e], k] for local diagonal
  * tiles).  dC: device M x N of dt (F32/BF16 with F32 dA, or F64 with F64 dA).  The plan's
  * schedule options pick the kernel.  Unless pipeline is 5 or persistent is set, BF16 rows of 256
- * or 512 bytes reduce each dot product through a shared-memory tile and FP32 rows of 512 bytes
- * through a 4-wide shuffle butterfly, both within 48 registers (40 warps per SM); pipeline 6
- * takes the tile for FP32 rows of 256/512 bytes too.  Other rows, pipeline 5 and persistent mode
- * use an 8-wide shuffle butterfly at 64 registers.  Each kernel sums in a fixed order, so dA is
- * deterministic for a given kernel. */
+ * or 512 bytes and FP32 rows of 256 bytes reduce each dot product through a shared-memory tile,
+ * FP32 rows of 512 bytes through a 4-wide shuffle butterfly, both within 48 registers (40 warps
+ * per SM, items taken from a counter in the plan); pipeline 6 takes the tile for FP32 rows of 512
+ * bytes too.  Other rows, pipeline 5 and persistent mode use an 8-wide shuffle butterfly at 64
+ * registers.  Each kernel sums in a fixed order, so dA is deterministic for a given kernel. */
 shiro_status shiro_sddmm(shiro_plan_t plan, const void* dC, int64_t lddc, const void* Bpack,
                          int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
                          void* dA, void* stream);

@@ -2,8 +2,8 @@
 // (a sampled dense-dense product on A's pattern, reading B through the packed rows), and the
 // backward entry point that adds dB = A^T dC through the transposed plan.
 //
-// One warp per work item (the SpMM schedule).  BF16 rows of 256 or 512 bytes and FP32 rows of 512
-// bytes take the 48-register kernels of sddmm_lean.cuh.  The kernel here takes the other shapes,
+// One warp per work item (the SpMM schedule).  BF16 rows of 256 or 512 bytes and FP32 rows of 256
+// or 512 bytes take the 48-register kernels of sddmm_lean.cuh.  The kernel here takes the other shapes,
 // persistent mode and pipeline 5: a batch of up to 32
 // nonzeros is taken as four sub-batches of 8, every lane forms its slice of the 8 dot products, a
 // butterfly reduction (4+2+1 shuffles, then 2) completes them, and one more shuffle hands nonzero
@@ -34,6 +34,7 @@ struct SddmmParams {
   int64_t n_items;
   int32_t chunk;
   int32_t persistent;
+  int32_t* work;  // item counter of the persistent 48-register kernels (zeroed before launch)
 };
 
 template <typename TB, int VEC, int NCH, bool MASKED>
@@ -223,26 +224,41 @@ namespace shiro {
 template <typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& prm,
                                  cudaStream_t s) {
-  // 48-register kernels outside persistent mode and pipeline 5: BF16 rows of 256 or 512 bytes
-  // with the shared-memory tile reduction, FP32 rows of 512 bytes (N = 128) with the 4-wide
-  // shuffle butterfly; pipeline 6 takes the tile for FP32 rows of 256/512 bytes too.  Measured on
-  // R-MAT 2^20, 4x4 tiles (ms; 64-register shuffle kernel -> tile / 4-wide butterfly):
-  // BF16 N = 256 1.82 -> 1.20 / 1.20, BF16 N = 128 0.92 -> 0.88 / 0.88,
-  // FP32 N = 128 0.93 -> 1.00 / 0.887, FP32 N = 64 0.78 -> 0.82 / 0.81 (the tile competes with
-  // the gathers for L1 bandwidth; FP32 N = 64 keeps the 64-register kernel).
+  // 48-register kernels outside persistent mode and pipeline 5: BF16 rows of 256 or 512 bytes and
+  // FP32 rows of 256 bytes (N = 64) with the shared-memory tile reduction, FP32 rows of 512 bytes
+  // (N = 128) with the 4-wide shuffle butterfly (the tile with pipeline 6).  Measured on R-MAT
+  // 2^20, 4x4 tiles, with items from a counter (ms; 64-register kernel -> tile / butterfly):
+  // BF16 N = 256 1.81 -> 1.02 / 1.02, BF16 N = 128 0.92 -> 0.82 / 0.82, FP32 N = 128
+  // 0.93 -> 0.82 / 0.75 (the tile competes with the gathers for L1 bandwidth), FP32 N = 64
+  // 0.78 -> 0.72 / 0.78.
   if constexpr (!MASKED && NCH == 1 && !std::is_same<TB, double>::value &&
                 VEC * sizeof(TB) >= 8) {
     constexpr bool BF = std::is_same<TB, __nv_bfloat16>::value;
-    const bool tile = BF || P->opts.pipeline == 6;
+    const bool tile = BF || VEC == 2 || P->opts.pipeline == 6;
     const bool shfl = !BF && VEC == 4 && P->opts.pipeline != 6;  // FP32 N = 128 rows
     if (!prm.persistent && P->opts.pipeline != 5 && (tile || shfl)) {
-      const int64_t grid = (prm.n_items + 1) / 2;
+      int64_t grid = (prm.n_items + 1) / 2;
       if (grid <= 0) return SHIRO_OK;
-      if (grid > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+      if (grid > INT32_MAX || prm.n_items > INT32_MAX)
+        SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+      // SMs x resident blocks; the warps take items from a counter in the plan (measured against
+      // one item per warp, ms: FP32 N = 128 0.92 -> 0.75, BF16 N = 256 1.21 -> 1.02, BF16
+      // N = 128 0.88 -> 0.82, FP32 N = 64 with the tile 0.79 -> 0.72).
+      SddmmParams<TB> q = prm;
+      int per_sm = 0;
       if (tile)
-        k_sddmm_lean<TB, VEC, true><<<(unsigned)grid, 64, 0, s>>>(prm);
+        SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_sddmm_lean<TB, VEC, true>, 64, 0));
+      else
+        SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_sddmm_lean<TB, VEC, (BF || VEC != 4)>, 64, 0));
+      grid = std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * P->sm_count);
+      q.work = P->d_status + 2;
+      SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));
+      if (tile)
+        k_sddmm_lean<TB, VEC, true><<<(unsigned)grid, 64, 0, s>>>(q);
       else if constexpr (!BF && VEC == 4)
-        k_sddmm_lean<TB, VEC, false><<<(unsigned)grid, 64, 0, s>>>(prm);
+        k_sddmm_lean<TB, VEC, false><<<(unsigned)grid, 64, 0, s>>>(q);
       SHIRO_CUDA(cudaGetLastError());
       return SHIRO_OK;
     }

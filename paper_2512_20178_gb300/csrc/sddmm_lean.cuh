@@ -1,6 +1,7 @@
 // sddmm_lean.cuh -- dA[e] = <dC[row e], B[col e]> with a 48-register budget, so that 40 warps fit
-// on an SM (2-warp CTAs, 20 per SM) instead of 32.  Two ways to finish the dot products: a 4-wide
-// shuffle butterfly per step of 4 nonzeros (four partial registers), or a shared-memory tile:
+// on an SM (2-warp CTAs, 20 per SM) instead of 32; launched as SMs x 20 blocks whose warps take
+// items from a counter.  Two ways to finish the dot products: a 4-wide shuffle butterfly per step
+// of 4 nonzeros (four partial registers), or a shared-memory tile:
 //
 // Per batch of 32 nonzeros every lane forms its slice of each dot product (VEC products of its
 // dC slice and the gathered B slice) and stores it into a 32 x 32 shared-memory tile, row = the
@@ -185,10 +186,22 @@ __global__ void __launch_bounds__(64, SD_LEAN_MIN_BLOCKS) k_sddmm_lean(const Sdd
   __shared__ __align__(16) float s_red[TILE ? 2 : 1][TILE ? 32 * 32 : 1];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int64_t it = (int64_t)blockIdx.x * 2 + warp;
-  if (it >= p.n_items) return;
-  const Item item = p.items[it];
-  sddmm_lean_item<TB, VEC, TILE>(p, s_idx[warp], TILE ? s_red[warp] : nullptr, item, lane);
+  if (!p.work) {
+    const int64_t it = (int64_t)blockIdx.x * 2 + warp;
+    if (it >= p.n_items) return;
+    sddmm_lean_item<TB, VEC, TILE>(p, s_idx[warp], TILE ? s_red[warp] : nullptr, p.items[it],
+                                   lane);
+    return;
+  }
+  // Persistent form: every warp takes the next item from the counter until none is left.
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(p.work, 1);
+    it = __shfl_sync(FULLM, it, 0);
+    if ((int64_t)it >= p.n_items) break;
+    sddmm_lean_item<TB, VEC, TILE>(p, s_idx[warp], TILE ? s_red[warp] : nullptr, p.items[it],
+                                   lane);
+  }
 }
 
 }  // namespace shiro

@@ -174,11 +174,11 @@ def test_gcn_full_fp32_vs_oracle():
 @pytest.mark.parametrize("case", ["f32_n128", "f32_n64", "bf16_n128", "bf16_n256", "hub",
                                   "local_diag", "empty_rows", "ragged"])
 def test_sddmm_kernels(case):
-    """dA by every SDDMM kernel -- 48 registers with the shared-memory tile reduction (BF16
-    default, pipeline 6 for FP32), 48 registers with the 4-wide shuffle butterfly (FP32 N = 128
-    default) and 64 registers with the 8-wide butterfly (pipeline 5, persistent mode, FP32 N = 64)
-    -- within the oracle bound on the same inputs, including hub rows cut into chunks, 1D local
-    diagonal tiles read from B in place, empty rows and a ragged last batch."""
+    """dA by every SDDMM kernel -- 48 registers with the shared-memory tile reduction (BF16 and
+    FP32 N = 64 default, pipeline 6 for FP32 N = 128), 48 registers with the 4-wide shuffle
+    butterfly (FP32 N = 128 default) and 64 registers with the 8-wide butterfly (pipeline 5,
+    persistent mode) -- within the oracle bound on the same inputs, including hub rows cut into
+    chunks, 1D local diagonal tiles read from B in place, empty rows and a ragged last batch."""
     shiro = gu.lib()
     flags, dt, N = 0, torch.float32, 128
     A = synth.rmat(13, 12, 140)

@@ -1,6 +1,6 @@
 """Helpers of the GPU parity tests: inputs to the device, oracle comparisons, tolerances.
 
-Tolerance (the benchmark spec): FP32 SpMM within max scaled error 1e-5 of the FP64 oracle, the error of
+Tolerance: FP32 SpMM within max scaled error 1e-5 of the FP64 oracle, the error of
 element (i, k) being |C_ik - C64_ik| / sum_j |a_ij| |b_jk| (and exact zeros where the scale is 0).
 The same bound is applied to dB (scale sum |a_ij| |dC_ik|) and dA (scale sum_k |dC_ik| |B_jk|).
 BF16-stored operands are compared with the oracle run on the BF16-rounded values, which FP64

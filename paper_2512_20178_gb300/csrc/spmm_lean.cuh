@@ -7,7 +7,10 @@
 //   * the values of the rows in flight: read again from shared memory at the FMA;
 //   * per-lane row state: one word, the row's end relative to the item's first nonzero, 0 for
 //     rows that end nowhere (empty rows and lanes past the item's rows).
-// Rows are summed in the same order as the other pipelines, so C is bit-identical to them.
+// Rows are summed in the same order as the register-gather and copy pipelines, so C is
+// bit-identical to theirs.  k_spmm_lean runs one item per warp; k_spmm_lean_dyn runs SMs x 20
+// blocks whose warps take items from a counter in the plan, so that no warp waits for its block's
+// other warp.
 #pragma once
 
 #include "internal.cuh"

@@ -345,8 +345,8 @@ shiro_status shiro_batch_plan_create(int32_t G, const shiro_csr* graphs, const s
  * (*best receives it).  Candidates vary the row-group size (from the average row length), the
  * chunk size of long rows (only when some row is longer), the CTA size and the pipeline: register
  * gathers, plus lane groups for rows of 128 or 256 bytes, the per-lane copy ring for FP32/BF16
- * rows of 512 bytes to 2 KB and the 48-register gathers for FP32/BF16 rows of 128-512 bytes
- * (outside persistent mode); the persistent mode stays as set.  Candidates whose scratch
+ * rows of 512 bytes to 2 KB and the 48-register gathers for FP32/BF16 rows of 128-512 bytes;
+ * the persistent mode stays as set.  Candidates whose scratch
  * does not fit scratch_bytes are skipped.  Synchronises `stream`. */
 shiro_status shiro_autotune(shiro_plan_t plan, const void* Bpack, int64_t ldp, const void* B,
                             int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,

@@ -23,7 +23,8 @@
  *     Nothing aborts or traps.  Device-side detection (e.g. a malformed CSR) sets a status word
  *     in the plan that plan creation or shiro_plan_check() reads back.
  *   - A plan may be used by one stream at a time: calls on the same plan must not overlap on the
- *     GPU (long rows use per-plan arrival counters).
+ *     GPU (long rows use per-plan arrival counters, and the counter-form kernels a per-plan work
+ *     counter that a memset node zeroes before each launch).
  */
 #ifndef SHIRO_H
 #define SHIRO_H

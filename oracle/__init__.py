@@ -281,13 +281,20 @@ def tile_graph(A, P: Plan, t: int):
     return r1 - r0, int(P.tile_ncols[t]), np.array(ptr, np.int64), np.array(adj, np.int32)
 
 
-def scaled_error(C, C64, S) -> float:
-    """max over elements of |C - C64| / S, where S = 0 requires C == 0 (returns inf otherwise)."""
-    C = np.asarray(C, dtype=np.float64)
-    d = np.abs(C - C64)
-    z = S == 0
-    if np.any(d[z] != 0):
-        return float("inf")
-    with np.errstate(divide="ignore", invalid="ignore"):
-        r = np.where(z, 0.0, d / np.where(z, 1.0, S))
-    return float(r.max()) if r.size else 0.0
+def scaled_error(C, C64, S, per_row: bool = False):
+    """Maximum over elements of |C - C64| / S, where S = 0 requires C == 0 exactly (the element
+    then counts 0, else +inf) and a NaN counts +inf (see oracle_scaled_error).  C may be any
+    float dtype (converted to FP64 exactly).  With per_row, returns the per-row maxima instead."""
+    C = _f64(C)
+    C64 = _f64(C64)
+    S = _f64(S)
+    if C.ndim == 1:
+        C, C64, S = C[:, None], C64[:, None], S[:, None]
+    if not (C.shape == C64.shape == S.shape):
+        raise ValueError(f"shape mismatch {C.shape} {C64.shape} {S.shape}")
+    n, N = C.shape
+    rm = np.zeros(max(n, 1), dtype=np.float64)
+    f = lib().oracle_scaled_error
+    f.restype = ctypes.c_double
+    worst = float(f(_i64(n), _i32(N), _p(C), _i64(N), _p(C64), _i64(N), _p(S), _i64(N), _p(rm)))
+    return rm[:n].copy() if per_row else worst

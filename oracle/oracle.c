@@ -20,6 +20,8 @@
  *   - C = A B (Sec. 2.1) summed in FP64, both directly from B and through the packed rows;
  *   - the backward pieces dB = A^T dC and dA_ij = <dC_i,:, B_j,:> on A's pattern, and the
  *     CSR transpose with rows of A^T in ascending order of A's row index;
+ *   - the per-element scale S = |A| |B| and the scaled error |C - C64| / S that turns a result
+ *     into pass or fail (the tolerance is stated on C = A B, Sec. 2.1);
  *   - the maximum matching of a tile's row-column graph, whose size is the minimum vertex cover
  *     mu of the joint row-column strategy (Sec. 5.3, Eq. 7-8; Koenig's theorem);
  *   - the minimum weighted vertex cover of that graph through the flow network and minimum cut
@@ -224,6 +226,35 @@ void oracle_abs_scale(int64_t M, const int64_t* rowptr, const int32_t* col, cons
       for (int32_t k = 0; k < N; ++k) s[k] += a * fabs(b[k]);
     }
   }
+}
+
+/* The tolerance of every parity comparison (the per-element scaled error of a result against
+ * the FP64 definition of C = A B, Sec. 2.1): for element (i, k) of an nrows x N result,
+ *   err_ik = |C_ik - C64_ik| / S_ik,   S_ik = sum_j |a_ij| |b_jk|   (from oracle_abs_scale),
+ * and where S_ik == 0 every term of the sum is 0, so C_ik must be exactly 0 (err 0) or the
+ * element fails (err +inf).  A NaN in C fails too.  Returns the maximum over all elements;
+ * row_max (nullable) receives the maximum of each row.  C, C64 and S are row-major with row
+ * strides ldc, ld64 and lds. */
+double oracle_scaled_error(int64_t nrows, int32_t N, const double* C, int64_t ldc,
+                           const double* C64, int64_t ld64, const double* S, int64_t lds,
+                           double* row_max) {
+  double worst = 0.0;
+  for (int64_t i = 0; i < nrows; ++i) {
+    double rmax = 0.0;
+    for (int32_t k = 0; k < N; ++k) {
+      const double c = C[i * ldc + k];
+      const double s = S[i * lds + k];
+      const double d = fabs(c - C64[i * ld64 + k]);
+      double r;
+      if (isnan(d)) r = INFINITY;
+      else if (s == 0.0) r = (c == 0.0) ? 0.0 : INFINITY;
+      else r = d / s;
+      if (r > rmax) rmax = r;
+    }
+    if (row_max) row_max[i] = rmax;
+    if (rmax > worst) worst = rmax;
+  }
+  return worst;
 }
 
 /* dB = A^T dC (the gradient of C = A B with respect to B): dB[j,k] = sum over nonzeros e with

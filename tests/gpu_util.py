@@ -115,11 +115,22 @@ def sampled_rows_error(A, B_host, C_rows, rows):
     Bs = np.asarray(B_host[ucols]) if len(ucols) else np.zeros((1, B_host.shape[1]), np.float32)
     C64 = oracle.spmm(S, Bs)
     Sc = oracle.abs_scale(S, Bs)
-    C = np.asarray(C_rows, dtype=np.float64)
-    d = np.abs(C - C64)
-    zero = Sc == 0
-    if np.any(d[zero] != 0):
-        return np.full(len(rows), np.inf)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        r = np.where(zero, 0.0, d / np.where(zero, 1.0, Sc))
-    return r.max(axis=1) if r.size else np.zeros(len(rows))
+    return oracle.scaled_error(np.asarray(C_rows), C64, Sc, per_row=True)
+
+
+def sampled_sddmm_error(A, dC_host, B_host, dA_vals, es):
+    """Maximum scaled error of the SDDMM values dA_vals (host array of all nnz) at the sampled
+    nonzeros es against the FP64 oracle, on a sub-problem with one row per sampled nonzero: row r
+    holds nonzero es[r] of A (its column remapped into the distinct sampled columns), so the
+    oracle's dA of that row is <dC[row(es[r])], B[col(es[r])]>.  The scale is the same SDDMM on
+    |dC| and |B|."""
+    es = np.asarray(es, dtype=np.int64)
+    rows_e = A.row_ids()[es]
+    ucols, local = np.unique(A.col[es], return_inverse=True)
+    S = synth.CSR(len(es), max(1, len(ucols)), np.arange(len(es) + 1, dtype=np.int64),
+                  local.astype(np.int32), A.val[es])
+    G = np.asarray(dC_host[rows_e])
+    Bs = np.asarray(B_host[ucols])
+    ref = oracle.sddmm(S, G, Bs)
+    sc = oracle.sddmm(S, np.abs(G), np.abs(Bs))
+    return oracle.scaled_error(np.asarray(dA_vals)[es], ref, sc)

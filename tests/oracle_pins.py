@@ -401,8 +401,87 @@ def check_fig1_weighted_cover():
     assert flow == expect["min_cover"][0] == int(cr.sum() + cc.sum())
 
 
+def check_scaled_error_hand_cases():
+    """The error metric every parity verdict goes through (the tolerance stated on C = A B,
+    Sec. 2.1: |C_ik - C64_ik| / sum_j |a_ij||b_jk|, exact zeros where that scale is 0), on triples
+    whose answer is worked out by hand.  The maximum sits where C < C64 and where S differs from
+    |C64|, so a signed difference or a division by |C64| lands elsewhere."""
+    inf = float("inf")
+    C, C64, S = [[1.0, 2.0, 3.0]], [[1.0, 2.5, 2.0]], [[2.0, 4.0, 16.0]]
+    # element errors 0, 0.5 / 4, 1 / 16: the maximum is 0.125, exactly representable.
+    assert oracle.scaled_error(C, C64, S) == 0.125, "known maximum element"
+    assert oracle.scaled_error([[0.0, -0.0]], [[0.0, 0.0]], [[0.0, 0.0]]) == 0.0, \
+        "S = 0 and C = 0 must count 0"
+    assert oracle.scaled_error([[1e-30, 0.0]], [[0.0, 0.0]], [[0.0, 1.0]]) == inf, \
+        "S = 0 and C != 0 must fail"
+    # Mixed rows: element errors (1/16, 0) and (0, 1/4); the maximum is 0.25 (a mean would be
+    # 5/64, a per-row mean 1/8), the per-row maxima 1/16 and 1/4.
+    C, C64, S = [[1.0, 1.0], [10.0, 10.0]], [[1.5, 1.0], [10.0, 10.25]], [[8.0, 1.0], [1.0, 1.0]]
+    assert oracle.scaled_error(C, C64, S) == 0.25, "maximum over mixed rows"
+    rm = oracle.scaled_error(C, C64, S, per_row=True)
+    assert list(rm) == [0.0625, 0.25], "per-row maxima"
+    assert oracle.scaled_error([[float("nan")]], [[1.0]], [[1.0]]) == inf, "NaN must fail"
+    assert oracle.scaled_error(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros((0, 3))) == 0.0
+    # 1-D results (SDDMM values): the same metric per nonzero.
+    assert oracle.scaled_error([3.0, -1.0], [2.0, -1.0], [8.0, 2.0]) == 0.125
+
+
+def check_scaled_error_fp32_bounds():
+    """Facts of floating-point arithmetic the metric must reproduce on real products: the FP64
+    result rounded once to FP32 has scaled error at most 2^-24 (|fl(x) - x| <= u |x| <= u S), and
+    a plain FP32 sum of a row's FP32 products in CSR order has scaled error at most
+    gamma_n = n u / (1 - n u) for n nonzeros in the row (the dot-product bound of Higham, Accuracy
+    and Stability of Numerical Algorithms, Sec. 3.1), and above 0 somewhere."""
+    u = 2.0 ** -24
+    A = synth.random_small(64, 96, 0.3, 17, empty_rows=4)
+    B = synth.dense_normal(A.K, 16, 18)
+    C64 = oracle.spmm(A, B)
+    S = oracle.abs_scale(A, B)
+    assert oracle.scaled_error(C64.astype(np.float32), C64, S) <= u
+    C32 = np.zeros((A.M, 16), dtype=np.float32)
+    for i in range(A.M):
+        acc = np.zeros(16, dtype=np.float32)
+        for e in range(int(A.rowptr[i]), int(A.rowptr[i + 1])):
+            acc = (acc + np.float32(A.val[e]) * B[A.col[e]]).astype(np.float32)
+        C32[i] = acc
+    rm = oracle.scaled_error(C32, C64, S, per_row=True)
+    n = np.diff(A.rowptr)
+    gamma = n * u / (1 - n * u)
+    assert np.all(rm <= gamma), "FP32 sum beyond the dot-product error bound"
+    assert rm.max() > 0, "an FP32 sum of these rows is inexact somewhere"
+    assert np.all(rm[n == 0] == 0), "empty rows are exact"
+
+
+def check_volumes_exact():
+    """Eq. 1: a tile's block volume is the size in bytes of the block of B owned by the tile's
+    column process, B^(q) = rows [k_q, k_(q+1)) of B; summed over the tiles of one row block it
+    is the whole of B.  Ragged custom bounds with P_r != P_c, and every element size."""
+    A = synth.random_small(13, 17, 0.4, 9)
+    rb = np.array([0, 5, 6, 13], np.int64)
+    cb = np.array([0, 3, 4, 11, 17], np.int64)
+    P = oracle.plan(A, 3, 4, rb=rb, cb=cb)
+    for N, dt in [(5, np.float32), (3, np.int16), (2, np.float64)]:
+        B = np.zeros((A.K, N), dtype=dt)
+        vb, vc = P.volumes(N, B.itemsize)
+        for p in range(3):
+            for q in range(4):
+                assert vb[p * 4 + q] == B[cb[q]:cb[q + 1]].nbytes, "V_block != bytes of B^(q)"
+            assert vb[p * 4:(p + 1) * 4].sum() == B.nbytes, "V_block over a row block != |B|"
+        assert np.all(vc <= vb)
+    g = [synth.random_small(m, m, 0.5, 60 + m) for m in (2, 7, 4)]
+    D = np.zeros((13, 13), dtype=np.float32)
+    b = np.array([0, 2, 9, 13], np.int64)
+    for t, gr in enumerate(g):
+        D[b[t]:b[t + 1], b[t]:b[t + 1]] = dense_of(gr)
+    Pd = oracle.plan(synth.from_dense(D), 3, 3, rb=b, cb=b, diag_only=True)
+    B = np.zeros((13, 4), dtype=np.float32)
+    vb, _ = Pd.volumes(4, 4)
+    assert [int(x) for x in vb] == [B[b[t]:b[t + 1]].nbytes for t in range(3)], "diag-only V_block"
+
+
 ALL_CHECKS = [check_weighted_cover_bruteforce, check_weighted_cover_special_cases,
               check_fig1_weighted_cover, check_matching_is_min_cover, check_fig1_joint_cover, check_spmm_dense, check_spmm_exact_structures, check_plan_bruteforce,
               check_uniform_bounds, check_plan_diag_only, check_pack_and_packed_spmm,
               check_transpose_and_rows, check_backward_dense, check_abs_scale, check_fig1_golden,
-              check_er_band]
+              check_er_band, check_scaled_error_hand_cases, check_scaled_error_fp32_bounds,
+              check_volumes_exact]

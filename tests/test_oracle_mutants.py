@@ -25,6 +25,17 @@ MUTANTS = {
     "cut_read_flipped": ("cover_col[v] = (uint8_t)(via[1 + nL + v] != -2);", "cover_col[v] = (uint8_t)(via[1 + nL + v] == -2);"),
     "no_residual_twin": ("cap[via[x] ^ 1] += b;", "(void)0;"),
     "source_capacity_wrong": ("ORACLE_ARC(s, 1 + u, w_row[u]);", "ORACLE_ARC(s, 1 + u, w_row[u] + (u == 0));"),
+    "scaled_error_plus_one": ("else r = d / s;", "else r = d / (s + 1.0);"),
+    "scaled_error_zero_rule_dropped": ("else if (s == 0.0) r = (c == 0.0) ? 0.0 : INFINITY;",
+                                       "else if (s == 0.0) r = 0.0;"),
+    "scaled_error_mean": ("if (r > rmax) rmax = r;", "rmax += r / (double)N;"),
+    "scaled_error_relative_to_c64": ("else r = d / s;", "else r = d / fabs(C64[i * ld64 + k]);"),
+    "scaled_error_signed": ("const double d = fabs(c - C64[i * ld64 + k]);",
+                            "const double d = c - C64[i * ld64 + k];"),
+    "volumes_width_off_by_one": ("v_block[t] = (cb[q + 1] - cb[q]) * (int64_t)N * sz;",
+                                 "v_block[t] = (cb[q + 1] - cb[q] + 1) * (int64_t)N * sz;"),
+    "volumes_q_of_row_block": ("int32_t q = diag_only ? t : t % Pc;\n    v_block",
+                               "int32_t q = diag_only ? t : t / Pc;\n    v_block"),
     "matching_no_flip": ("for (int32_t l = d - 1; l >= 0; --l) matchR[sv[l]] = su[l];", "(void)sv;"),
 }
 

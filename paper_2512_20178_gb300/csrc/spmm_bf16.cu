@@ -1,0 +1,12 @@
+// spmm_bf16.cu -- the SpMM kernels instantiated for __nv_bfloat16 storage (float values).
+#include "spmm_kernels.cuh"
+
+namespace shiro {
+
+shiro_status spmm_bf16(const shiro_plan_s* P, const void* Bpack, int64_t ldp, const void* B,
+                        int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
+                        uint32_t flags, void* scratch, cudaStream_t s) {
+  return spmm_typed<float, __nv_bfloat16>(P, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, s);
+}
+
+}  // namespace shiro

@@ -95,11 +95,18 @@ __global__ void __launch_bounds__(256, 4) k_spmm_grouped(const SpmmParams<TV, TB
       // Partial of this chunk (group 0), arrival count, ordered sum by the last chunk.
       TA* part = p.scratch + (int64_t)slot * p.N + lane * VEC;
       if (lane < 32 / G) store_acc_cg<TA, VEC>(part, acc);
+      // Release (fence, then a warp barrier before lane 0's arrival count) and acquire (lane 0
+      // fences after the count, a warp barrier before any lane reads the other partials).
       __threadfence();
+      __syncwarp();
       const int32_t lr = __ldg(p.slot_lr + slot);
       const LongRow L = p.lr[lr];
       int old = 0;
-      if (lane == 0) old = atomicAdd(p.counters + lr, 1);
+      if (lane == 0) {
+        old = atomicAdd(p.counters + lr, 1);
+        __threadfence();
+      }
+      __syncwarp();
       old = __shfl_sync(0xffffffffu, old, 0);
 #pragma unroll
       for (int v = 0; v < VEC; ++v) acc[v] = 0;

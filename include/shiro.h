@@ -172,11 +172,17 @@ shiro_status shiro_plan_query(shiro_plan_t plan, shiro_plan_info* info);
 shiro_status shiro_plan_tile_stats(shiro_plan_t plan, int64_t* tile_nnz, int64_t* tile_nrows,
                                    int64_t* tile_ncols, int64_t* tile_cols_ptr, int64_t* pack_ptr);
 
-/* Communication volumes in bytes for N columns of dtype dt (host arrays of n_tiles entries):
- * v_block[t] = (width of column block q) * N * sz (Eq. 1), v_col[t] = |Cols(A^(p,q))| * N * sz
- * (Eq. 2), v_row[t] = |Rows(A^(p,q))| * N * sz (Eq. 3).  Any pointer may be NULL. */
-shiro_status shiro_plan_volumes(shiro_plan_t plan, int32_t N, shiro_dtype dt, int64_t* v_block,
-                                int64_t* v_col, int64_t* v_row);
+/* Communication volumes in bytes for N columns (host arrays of n_tiles entries), B stored as
+ * b_dt and partial C rows exchanged as c_dt (the accumulator type: F32 for F32 or BF16 B, F64 for
+ * F64 B):
+ *   v_block[t] = (width of column block q) * N * sz(b_dt)   (Eq. 1: the whole block B^(q));
+ *   v_col[t]   = |Cols(A^(p,q))| * N * sz(b_dt)              (Eq. 2: the B rows the tile names);
+ *   v_row[t]   = |Rows(A^(p,q))| * N * sz(c_dt)              (Eq. 3: one partial C row per row
+ *                                                             of the tile holding a nonzero).
+ * Diagonal tiles of a LOCAL_DIAG plan are local computation (Sec. 2.2) and report 0 in all three.
+ * Any output pointer may be NULL. */
+shiro_status shiro_plan_volumes(shiro_plan_t plan, int32_t N, shiro_dtype b_dt, shiro_dtype c_dt,
+                                int64_t* v_block, int64_t* v_col, int64_t* v_row);
 
 /* Joint row-column strategy (Sec. 5.2-5.3) for every tile: a minimum vertex cover of the bipartite
  * graph rows--columns whose edges are the tile's nonzeros (uniform costs, Sec. 5.4: the cover size
@@ -295,7 +301,9 @@ shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const
  * split rows go to one static device array of SHIRO_NOALLOC_SCRATCH_BYTES (16 MiB) inside the
  * library, which every GPU that loads the library holds until the process exits.  A plan whose
  * shiro_spmm_scratch(plan, N, dt) exceeds that size is rejected with
- * SHIRO_ERR_INSUFFICIENT_WORKSPACE (16 MiB holds 32,768 split-row chunks at N = 128 in FP32).
+ * SHIRO_ERR_INSUFFICIENT_WORKSPACE (16 MiB holds up to 32,767 split-row chunks at N = 128 in
+ * FP32: the size check keeps the 256-byte alignment margin of shiro_spmm_scratch).  The plan must
+ * belong to the current device (SHIRO_ERR_INVALID_ARG otherwise).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture begins.  All calls on a device
  * share the one array, which keeps the last call's partial sums (nothing in it has to start at

@@ -116,12 +116,17 @@ class Plan:
         pack_src = np.concatenate(src).astype(np.int32) if src else np.zeros(0, np.int32)
         return pack_ptr, pack_src
 
-    def volumes(self, N: int, sz: int):
+    def volumes(self, N: int, sz: int, szc: int = 4, local_diag: bool = False):
+        """(V_block, V_col, V_row) per tile in bytes (Eq. 1-3): B elements of sz bytes, partial C
+        elements of szc bytes; local diagonal tiles report 0."""
         vb = np.zeros(self.T, dtype=np.int64)
         vc = np.zeros(self.T, dtype=np.int64)
+        vr = np.zeros(self.T, dtype=np.int64)
         lib().oracle_volumes(_i32(self.Pr), _i32(self.Pc), ctypes.c_int(int(self.diag_only)),
-                             _p(self.cb), _p(self.tile_ncols), _i32(N), _i32(sz), _p(vb), _p(vc))
-        return vb, vc
+                             ctypes.c_int(int(local_diag)), _p(self.cb), _p(self.tile_ncols),
+                             _p(self.tile_nrows), _i32(N), _i32(sz), _i32(szc), _p(vb), _p(vc),
+                             _p(vr))
+        return vb, vc, vr
 
 
 def plan(A, Pr: int, Pc: int, rb=None, cb=None, diag_only: bool = False) -> Plan:

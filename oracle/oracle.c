@@ -137,15 +137,21 @@ int oracle_plan(int64_t M, int64_t K, const int64_t* rowptr, const int32_t* col,
   return 0;
 }
 
-/* Volumes of Eq. 1 and Eq. 2 for every tile, in bytes, for N columns of sz bytes. */
-void oracle_volumes(int32_t Pr, int32_t Pc, int diag_only, const int64_t* cb,
-                    const int64_t* tile_ncols, int32_t N, int32_t sz, int64_t* v_block,
-                    int64_t* v_col) {
+/* Volumes of Eq. 1, Eq. 2 and Eq. 3 for every tile, in bytes, for N columns: B elements of sz
+ * bytes (the block B^(q) for Eq. 1, the rows named by Cols for Eq. 2) and partial C elements of
+ * szc bytes (one partial row per row of Rows for Eq. 3).  With local_diag the diagonal tiles are
+ * the local computation of Sec. 2.2 and communicate nothing (0 bytes). */
+void oracle_volumes(int32_t Pr, int32_t Pc, int diag_only, int local_diag, const int64_t* cb,
+                    const int64_t* tile_ncols, const int64_t* tile_nrows, int32_t N, int32_t sz,
+                    int32_t szc, int64_t* v_block, int64_t* v_col, int64_t* v_row) {
   int32_t T = diag_only ? Pr : Pr * Pc;
   for (int32_t t = 0; t < T; ++t) {
+    int32_t p = diag_only ? t : t / Pc;
     int32_t q = diag_only ? t : t % Pc;
     v_block[t] = (cb[q + 1] - cb[q]) * (int64_t)N * sz;
     v_col[t] = tile_ncols[t] * (int64_t)N * sz;
+    v_row[t] = tile_nrows[t] * (int64_t)N * szc;
+    if (local_diag && p == q) v_block[t] = v_col[t] = v_row[t] = 0;
   }
 }
 

@@ -697,16 +697,21 @@ shiro_status shiro_plan_tile_stats(shiro_plan_t P, int64_t* tile_nnz, int64_t* t
   return SHIRO_OK;
 }
 
-shiro_status shiro_plan_volumes(shiro_plan_t P, int32_t N, shiro_dtype dt, int64_t* v_block,
-                                int64_t* v_col, int64_t* v_row) {
+shiro_status shiro_plan_volumes(shiro_plan_t P, int32_t N, shiro_dtype b_dt, shiro_dtype c_dt,
+                                int64_t* v_block, int64_t* v_col, int64_t* v_row) {
   if (!P || N < 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan or negative N");
-  const int64_t sz = (int64_t)dtype_size(dt);
+  auto known = [](shiro_dtype d) { return d == SHIRO_F32 || d == SHIRO_BF16 || d == SHIRO_F64; };
+  if (!known(b_dt) || !known(c_dt)) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "unknown dtype");
+  const int64_t szb = (int64_t)dtype_size(b_dt), szc = (int64_t)dtype_size(c_dt);
   const bool diag = P->flags & SHIRO_PLAN_DIAG_ONLY;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
   for (int32_t t = 0; t < P->T; ++t) {
+    const int32_t p = diag ? t : t / P->geo.Pc;
     const int32_t q = diag ? t : t % P->geo.Pc;
-    if (v_block) v_block[t] = (P->cb[q + 1] - P->cb[q]) * N * sz;
-    if (v_col) v_col[t] = P->tile_ncols[t] * N * sz;
-    if (v_row) v_row[t] = P->tile_nrows[t] * N * sz;
+    const bool none = local && p == q;  // a local diagonal tile communicates nothing
+    if (v_block) v_block[t] = none ? 0 : (P->cb[q + 1] - P->cb[q]) * N * szb;
+    if (v_col) v_col[t] = none ? 0 : P->tile_ncols[t] * N * szb;
+    if (v_row) v_row[t] = none ? 0 : P->tile_nrows[t] * N * szc;
   }
   return SHIRO_OK;
 }

@@ -66,7 +66,7 @@ SIGNATURES = [
     ("shiro_plan_destroy", None, [_vp]),
     ("shiro_plan_query", ctypes.c_int, [_vp, _P(shiro_plan_info)]),
     ("shiro_plan_tile_stats", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
-    ("shiro_plan_volumes", ctypes.c_int, [_vp, _i32, ctypes.c_int, _vp, _vp, _vp]),
+    ("shiro_plan_volumes", ctypes.c_int, [_vp, _i32, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     ("shiro_plan_joint", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_joint_weighted", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp]),
     ("shiro_plan_row_based", ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -256,10 +256,16 @@ class Plan:
                                              ("tile_nnz", "tile_nrows", "tile_ncols", "tile_cols_ptr", "pack_ptr")])
         return out
 
-    def volumes(self, N, dtype=torch.float32):
+    def volumes(self, N, dtype=torch.float32, c_dtype=None):
+        """(V_block, V_col, V_row) per tile in bytes (Eq. 1-3) for B stored as ``dtype`` and
+        partial C rows as ``c_dtype`` (default: the accumulator type, FP64 for FP64 B, else
+        FP32)."""
+        if c_dtype is None:
+            c_dtype = torch.float64 if dtype == torch.float64 else torch.float32
         T = self.info.n_tiles
         vb, vc, vr = (torch.zeros(T, dtype=torch.int64) for _ in range(3))
-        shiro_plan_volumes(self.handle, int(N), dtype_code(dtype), _ptr(vb), _ptr(vc), _ptr(vr))
+        shiro_plan_volumes(self.handle, int(N), dtype_code(dtype), dtype_code(c_dtype), _ptr(vb),
+                           _ptr(vc), _ptr(vr))
         return vb, vc, vr
 
     def joint(self, stream=None):

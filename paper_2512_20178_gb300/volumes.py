@@ -6,12 +6,12 @@ For every tile A^(p,q) of a plan this reports, in bytes for N columns:
   V_row    = |Rows(A^(p,q))| * N * sz_C                 (Eq. 3, row-based)
   V_joint  = cost of the minimum weighted vertex cover  (Eq. 9 / Sec. 5.3.3, joint)
 with sz_B the size of a B element and sz_C the size of a partial-C element (FP32 accumulators).
-When sz_B == sz_C the joint cover is the uniform one (Hopcroft-Karp + Koenig) and V_joint =
-mu * N * sz; otherwise it is the min cut with costs N * sz_C per row and N * sz_B per column.
-Local diagonal tiles of a LOCAL_DIAG (1D) plan communicate nothing and report 0 everywhere.
+The joint cover is the min cut of Sec. 5.3.3 with costs N * sz_C per row and N * sz_B per
+column (with sz_B == sz_C it is the uniform cover, mu * N * sz).  Local diagonal tiles of a
+LOCAL_DIAG (1D) plan communicate nothing and report 0 everywhere.
 
-Every number comes from the library (plan statistics and the cover solvers); this module only
-formats them.  Run as ``python -m paper_2512_20178_gb300.volumes --scale 20 --deg 16 --grid 4x4``
+Every number comes from the library (shiro_plan_volumes and the weighted cover solver); this
+module only formats them.  Run as ``python -m paper_2512_20178_gb300.volumes --scale 20 --deg 16 --grid 4x4``
 (needs a GPU: the plan is built on the device).
 """
 from __future__ import annotations
@@ -23,33 +23,19 @@ import numpy as np
 import torch
 
 SIZES = {"f32": 4, "bf16": 2, "f64": 8}
+DTYPES = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}
 
 
-def tile_volumes(plan, N: int, b_dtype: str = "f32", c_dtype: str = "f32", local_diag=False):
-    """Per-tile V_block, V_col, V_row and V_joint (int64 arrays of n_tiles) plus the joint cover."""
-    szb, szc = SIZES[b_dtype], SIZES[c_dtype]
-    st = plan.tile_stats()
-    T = plan.info.n_tiles
-    vb, _, _ = plan.volumes(N, {"f32": torch.float32, "bf16": torch.bfloat16,
-                                "f64": torch.float64}[b_dtype])
-    vb = vb.numpy().copy()
-    ncols = st["tile_ncols"].numpy().astype(np.int64)
-    nrows = st["tile_nrows"].numpy().astype(np.int64)
-    if szb == szc:
-        J = plan.joint()
-        vj = J["mu"].numpy().astype(np.int64) * N * szb
-    else:
-        J = plan.joint_weighted(N * szc, N * szb)
-        vj = J["cost"].numpy().astype(np.int64)
-    vc = ncols * N * szb
-    vr = nrows * N * szc
-    if local_diag:
-        Pc = plan.info.P_c
-        for t in range(T):
-            if t // Pc == t % Pc:
-                vb[t] = vc[t] = vr[t] = vj[t] = 0
-    return {"V_block": vb, "V_col": vc, "V_row": vr, "V_joint": vj,
-            "cover_rows": J["cover_rows"].numpy(), "cover_cols": J["cover_cols"].numpy()}
+def tile_volumes(plan, N: int, b_dtype: str = "f32", c_dtype: str = "f32"):
+    """Per-tile V_block, V_col, V_row (shiro_plan_volumes) and V_joint (the minimum weighted cover
+    of shiro_plan_joint_weighted with a row priced at one partial C row, N * sz_C bytes, and a
+    column at one B row, N * sz_B bytes), int64 arrays of n_tiles, plus the cover sizes.  Local
+    diagonal tiles of a LOCAL_DIAG plan are reported as 0 by the library."""
+    vb, vc, vr = plan.volumes(N, DTYPES[b_dtype], DTYPES[c_dtype])
+    J = plan.joint_weighted(N * SIZES[c_dtype], N * SIZES[b_dtype])
+    return {"V_block": vb.numpy(), "V_col": vc.numpy(), "V_row": vr.numpy(),
+            "V_joint": J["cost"].numpy(), "cover_rows": J["cover_rows"].numpy(),
+            "cover_cols": J["cover_cols"].numpy()}
 
 
 def format_matrix(name: str, v: np.ndarray, Pr: int, Pc: int, unit: float = 2**20) -> str:
@@ -63,9 +49,9 @@ def format_matrix(name: str, v: np.ndarray, Pr: int, Pc: int, unit: float = 2**2
     return "\n".join(lines)
 
 
-def report(plan, N: int, b_dtype="f32", c_dtype="f32", local_diag=False) -> dict:
+def report(plan, N: int, b_dtype="f32", c_dtype="f32") -> dict:
     Pr, Pc = plan.info.P_r, plan.info.P_c
-    V = tile_volumes(plan, N, b_dtype, c_dtype, local_diag)
+    V = tile_volumes(plan, N, b_dtype, c_dtype)
     tot = {k: int(V[k].sum()) for k in ("V_block", "V_col", "V_row", "V_joint")}
     text = "\n\n".join(format_matrix(k, V[k], Pr, Pc) for k in ("V_block", "V_col", "V_row", "V_joint"))
     red = {"joint_vs_col": 1 - tot["V_joint"] / max(1, tot["V_col"]),
@@ -98,7 +84,7 @@ def main(argv=None):
     val = torch.from_numpy(A.val).to(d)
     flags = shiro.SHIRO_PLAN_LOCAL_DIAG if a.local_diag else 0
     P = shiro.Plan.create(rp, col, val, A.M, A.K, Pr, Pc, flags=flags)
-    R = report(P, a.N, a.b_dtype, a.c_dtype, a.local_diag)
+    R = report(P, a.N, a.b_dtype, a.c_dtype)
     head = {"graph": a.graph, "scale": a.scale, "deg": a.deg, "nnz": int(A.nnz), "grid": a.grid,
             "local_diag": a.local_diag, "N": a.N, "b_dtype": a.b_dtype, "c_dtype": a.c_dtype}
     if a.json:

@@ -76,10 +76,11 @@ def assert_plan_matches(P, A, Pr, Pc, flags=0, rb=None, cb=None):
     if local:
         expect = np.where(p == q, -1 - A.col.astype(np.int64), expect)
     assert np.array_equal(ex["remap"].cpu().numpy(), expect.astype(np.int32)), "remap"
-    vb, vc, vr = P.volumes(32, torch.float32)
-    ob, oc = O.volumes(32, 4)
-    assert np.array_equal(vb.numpy(), ob) and np.array_equal(vc.numpy(), oc), "volumes"
-    assert np.array_equal(vr.numpy(), O.tile_nrows * 32 * 4)
+    for dt, sz in ((torch.float32, 4), (torch.bfloat16, 2)):
+        vb, vc, vr = P.volumes(32, dt)
+        ob, oc, orow = O.volumes(32, sz, 4, local)
+        assert np.array_equal(vb.numpy(), ob) and np.array_equal(vc.numpy(), oc), "volumes"
+        assert np.array_equal(vr.numpy(), orow), "V_row"
     return O
 
 

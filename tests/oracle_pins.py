@@ -118,9 +118,13 @@ def check_plan_bruteforce():
             assert sum(P.tile_ncols[p * Pc:(p + 1) * Pc]) == len(row_cols), \
                 "sum_q |Cols(A^(p,q))| != |Cols(A^(p,:))|"
         assert P.tile_cols_ptr[-1] <= min(A.nnz, Pr * A.K)
-        vb, vc = P.volumes(N, 4)
+        vb, vc, vr = P.volumes(N, 4)
         assert np.all(vb >= vc), "V_block < V_col"
-        assert np.array_equal(vc, P.tile_ncols * N * 4)
+        for t in range(P.T):
+            cs, rs, _ = ref[t]
+            # Eq. 2 and Eq. 3: bytes of the B rows the tile names, of its partial C rows.
+            assert vc[t] == np.zeros((len(cs), N), np.float32).nbytes, "V_col"
+            assert vr[t] == np.zeros((len(rs), N), np.float32).nbytes, "V_row"
 
 
 def check_uniform_bounds():
@@ -462,7 +466,8 @@ def check_volumes_exact():
     P = oracle.plan(A, 3, 4, rb=rb, cb=cb)
     for N, dt in [(5, np.float32), (3, np.int16), (2, np.float64)]:
         B = np.zeros((A.K, N), dtype=dt)
-        vb, vc = P.volumes(N, B.itemsize)
+        vb, vc, vr = P.volumes(N, B.itemsize, 8)
+        assert np.array_equal(vr, P.tile_nrows * np.zeros((1, N), np.float64).nbytes)
         for p in range(3):
             for q in range(4):
                 assert vb[p * 4 + q] == B[cb[q]:cb[q + 1]].nbytes, "V_block != bytes of B^(q)"
@@ -475,8 +480,16 @@ def check_volumes_exact():
         D[b[t]:b[t + 1], b[t]:b[t + 1]] = dense_of(gr)
     Pd = oracle.plan(synth.from_dense(D), 3, 3, rb=b, cb=b, diag_only=True)
     B = np.zeros((13, 4), dtype=np.float32)
-    vb, _ = Pd.volumes(4, 4)
+    vb, _, _ = Pd.volumes(4, 4)
     assert [int(x) for x in vb] == [B[b[t]:b[t + 1]].nbytes for t in range(3)], "diag-only V_block"
+    # 1D plan with local diagonal tiles (Sec. 2.2): those tiles send nothing, the others are
+    # unchanged.
+    Pq = oracle.plan(A, 3, 3)
+    full = Pq.volumes(4, 2)
+    loc = Pq.volumes(4, 2, local_diag=True)
+    for t in range(9):
+        for f, l in zip(full, loc):
+            assert l[t] == (0 if t // 3 == t % 3 else f[t]), "local diagonal tile volumes"
 
 
 ALL_CHECKS = [check_weighted_cover_bruteforce, check_weighted_cover_special_cases,

@@ -22,18 +22,18 @@ def test_volume_matrices(b_dtype, local):
     N = 32
     flags = shiro.SHIRO_PLAN_LOCAL_DIAG if local else 0
     P = gu.plan_of(A, 4, 4, flags)
-    R = volumes.report(P, N, b_dtype, "f32", local)
+    R = volumes.report(P, N, b_dtype, "f32")
     O = oracle.plan(A, 4, 4)
     szb = volumes.SIZES[b_dtype]
+    ob, oc, orow = O.volumes(N, szb, 4, local)
     V = {k: np.array(v) for k, v in R["tiles"].items()}
     for t in range(O.T):
         p, q = O.tile_pq(t)
         if local and p == q:
             assert all(V[k][t] == 0 for k in ("V_block", "V_col", "V_row", "V_joint"))
             continue
-        assert V["V_block"][t] == (O.cb[q + 1] - O.cb[q]) * N * szb
-        assert V["V_col"][t] == O.tile_ncols[t] * N * szb
-        assert V["V_row"][t] == O.tile_nrows[t] * N * 4
+        assert V["V_block"][t] == ob[t] and V["V_col"][t] == oc[t], "Eq. 1 / Eq. 2"
+        assert V["V_row"][t] == orow[t], "Eq. 3 (FP32 partial C rows, also for BF16 B)"
         nL, nR, ptr, adj = oracle.tile_graph(A, O, t)
         if szb == 4:
             assert V["V_joint"][t] == oracle.max_matching(nL, nR, ptr, adj) * N * 4

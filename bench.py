@@ -1,19 +1,28 @@
 """Benchmark of the sparsity-aware SpMM hot path on one GB300 (or N independent replicas).
 
-Workload (default): R-MAT CSR A 2^20 x 2^20, avg degree 16 (a,b,c,d = .57,.19,.19,.05,
-duplicates merged), FP32 values U(0,1), dense B 2^20 x 128 FP32 N(0,1), 4x4 logical tiles.
-One step = pack the B rows named by every tile's unique columns (Sec. 5.1 stage 3) + SpMM over
-the packed rows summed over the tiles of each row block (stage 5).  The plan (stage 1) is built
-once per pattern, as in the paper, and timed on its own.
+Workload (the JSON line's step): R-MAT CSR A 2^20 x 2^20, avg degree 16 (a,b,c,d =
+.57,.19,.19,.05, duplicates merged), FP32 values U(0,1), dense B 2^20 x 128 FP32 N(0,1), 4x4
+logical tiles.  One step = pack the B rows named by every tile's unique columns (Sec. 5.1 stage 3)
++ SpMM over the packed rows summed over the tiles of each row block (stage 5).  The plan (stage 1)
+is built once per pattern, as in the paper, and timed on its own.
 
+Bytes are algorithmic, each counted once:
+  SpMM  (M+1)*8 + nnz*(4 col + 4 val) + R*N*sz (packed rows) + M*N*4 (C);
+  pack  2*R*N*sz + R*4 (gather read + packed write + index), R = packed rows.
 The JSON line reports:
-  value     -- algorithmic GB/s of the step: pack 2*R*N*4 + R*4, SpMM (M+1)*8 + nnz*8 + R*N*4 +
-               M*N*4 bytes (R = packed rows), over the device time of K steps (CUDA events);
-  roofline  -- the SpMM kernel alone: its algorithmic bytes / its mean launch time vs the
-               measured HBM copy bandwidth;
-  e2e       -- the same bytes over steps that also copy B from pinned host memory and C back;
-  cpu_baseline -- the FP64 C oracle on a strided row sample, on this host's cores;
-  forms     -- BF16-stored B, the backward (dB = A^T dC, dA by SDDMM) and fwd+bwd time.
+  value     -- SpMM bytes / step time (pack + SpMM): the SpMM's numerator over the whole step,
+               the conservative reading of the headline; GB/s;
+  roofline  -- the SpMM kernel alone: SpMM bytes / its mean launch time (CUDA events on its
+               stream) vs the measured HBM copy bandwidth; with two ceilings: the HBM time of
+               those bytes, and the same kernel, schedule and gather count on a matrix whose
+               columns are folded so that every packed row stays in L2 (the gather-rate bound);
+  e2e       -- the same SpMM bytes over steps that also copy B from pinned host memory and C back;
+  forms     -- every other configuration, each with its time, algorithmic GB/s and fraction of
+               the HBM peak: the backward (dB = A^T dC, dA by SDDMM), BF16-stored B, an N sweep,
+               the precision workload (R-MAT 2^22, BF16 N = 256), the GCN layer fwd + bwd, 512
+               batched graphs in one CUDA graph (tuned and default schedules), the small 1D ER
+               case; clocks are sampled over all of them;
+  cpu_baseline -- the FP64 C oracle on a strided row sample, on this host's cores.
 Inputs are larger than L2 (B 512 MB, packed B 650 MB, C 512 MB), so no L2 flush is needed.
 
 --impl reference times the FP64 CPU oracle (the reference arm here; the paper ships no kernels).
@@ -22,6 +31,7 @@ With N > 1 (torchrun) every rank runs its own replica (weak scaling, no collecti
 from __future__ import annotations
 
 import argparse
+import glob
 import hashlib
 import json
 import os
@@ -35,11 +45,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "SpMM GB/s (pack + SpMM, algorithmic bytes) vs HBM roofline"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "spmm_rmat20_n128_traffic.json")
-KERNEL_SOURCES = ["paper_2512_20178_gb300/csrc/spmm.cu", "paper_2512_20178_gb300/csrc/vec.cuh",
-                  "paper_2512_20178_gb300/csrc/internal.cuh",
-                  "paper_2512_20178_gb300/csrc/spmm_lean.cuh"]
+METRIC = "SpMM GB/s & GFLOP/s (2*nnz*N) vs HBM roofline; fwd+bwd ms, FP32 vs BF16"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+# Every source of the library: a stored DRAM-traffic figure is used only while all are unchanged.
+KERNEL_SOURCE_GLOBS = ["paper_2512_20178_gb300/csrc/*.cu", "paper_2512_20178_gb300/csrc/*.cuh",
+                       "include/shiro.h"]
+FORMS = ("backward", "bf16", "nsweep", "cusparse", "precision", "gcn", "batch", "er")
 
 
 def spmm_kernel(N, sz):
@@ -52,7 +63,7 @@ def spmm_kernel(N, sz):
     return "k_spmm"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
@@ -62,24 +73,50 @@ def parse():
     ap.add_argument("--deg", type=int, default=16)
     ap.add_argument("--N", type=int, default=128)
     ap.add_argument("--tiles", type=int, default=4)
-    ap.add_argument("--seed", type=int, default=2)
-    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--seed", type=int, default=None,
+                    help="generator seed (default: 3 for the R-MAT 2^22 degree-32 precision "
+                         "workload, else 2)")
+    ap.add_argument("--forms", default="all",
+                    help="comma-separated subset of " + ",".join(FORMS) + ", or all / none")
+    ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"],
                     help="storage of B (and of the packed rows); accumulation is FP32 either way")
     ap.add_argument("--er", action="store_true",
-                    help="time the small 1D case instead: Erdos-Renyi 4096 x 4096, avg degree 8, "
-                         "values U(-1, 1), B 4096 x 32, P = 4 row blocks with local diagonal tiles "
-                         "(L2-resident and launch-bound: reported, not roofline-judged)")
+                    help="time only the small 1D case: Erdos-Renyi 4096 x 4096, avg degree 8, "
+                         "values U(-1, 1), B 4096 x 32, P = 4 row blocks with local diagonal tiles")
     ap.add_argument("--gcn", action="store_true",
-                    help="time the GCN layer instead: Y = A_hat (X W), A_hat the symmetric-normalised "
-                         "R-MAT 2^scale graph with self loops, X n x 256, W 256 x N, fwd + bwd "
-                         "through the autograd wrapper")
+                    help="time only the GCN layer: Y = A_hat (X W), A_hat the symmetric-normalised "
+                         "R-MAT 2^scale graph with self loops, X n x 256, W 256 x N, fwd + bwd")
     ap.add_argument("--batch", type=int, default=0,
-                    help="time the batched form instead: this many R-MAT graphs, n ~ U{100..20000}, "
+                    help="time only the batched form: this many R-MAT graphs, n ~ U{100..20000}, "
                          "degree log-uniform [4, 40], B n x N in BF16, one CUDA-graph replay per step")
-    return ap.parse_args()
+    ap.add_argument("--traffic-from", default=None, metavar="CSV",
+                    help="write the DRAM-traffic record of profiles/traffic.json from an ncu "
+                         "'--page raw --csv' export (with --kernel and --workload) and exit")
+    ap.add_argument("--kernel", default=None, help="kernel instantiation of --traffic-from")
+    ap.add_argument("--workload", default=None, help="workload name of --traffic-from")
+    ap.add_argument("--command", default=None, help="the ncu command of --traffic-from")
+    a = ap.parse_args(argv)
+    if a.no_forms:
+        a.forms = "none"
+    if a.seed is None:
+        a.seed = 3 if (a.scale, a.deg) == (22, 32) else 2
+    return a
+
+
+def forms_of(args):
+    if args.forms in ("all", ""):
+        return set(FORMS)
+    if args.forms == "none":
+        return set()
+    s = {f.strip() for f in args.forms.split(",") if f.strip()}
+    bad = s - set(FORMS)
+    if bad:
+        raise SystemExit(f"unknown forms {sorted(bad)}")
+    return s
 
 
 def workload(args):
@@ -89,20 +126,35 @@ def workload(args):
     return A, B
 
 
-def config(args, A, extra=None):
-    c = {"workload": f"rmat{args.scale}_deg{args.deg}_N{args.N}_{args.tiles}x{args.tiles}_{args.dtype}",
-         "M": A.M, "K": A.K, "nnz": A.nnz, "N": args.N, "tiles": f"{args.tiles}x{args.tiles}",
-         "rmat": [0.57, 0.19, 0.19, 0.05], "seed": args.seed,
-         "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
-    if extra:
-        c.update(extra)
-    return c
+def workload_name(scale, deg, N, tiles, dtype):
+    return f"rmat{scale}_deg{deg}_N{N}_{tiles}x{tiles}_{dtype}"
+
+
+def config(args, A):
+    """The workload, identical on both arms (no measured or plan-dependent keys)."""
+    return {"workload": workload_name(args.scale, args.deg, args.N, args.tiles, args.dtype),
+            "M": A.M, "K": A.K, "nnz": A.nnz, "N": args.N, "tiles": f"{args.tiles}x{args.tiles}",
+            "rmat": [0.57, 0.19, 0.19, 0.05], "seed": args.seed, "storage": args.dtype,
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+
+
+def spmm_bytes(M, nnz, R, N, sz):
+    """Algorithmic bytes of one SpMM over R packed rows of N sz-byte elements (FP32 C)."""
+    return (M + 1) * 8 + nnz * 8 + R * N * sz + M * N * 4
+
+
+def pack_bytes(R, N, sz):
+    """Algorithmic bytes of one pack of R rows: gather read, packed write, source index."""
+    return 2 * R * N * sz + R * 4
+
+
+def sddmm_bytes(M, nnz, R, N, sz):
+    """Algorithmic bytes of one SDDMM: A's pattern, dC rows, packed B rows, dA values."""
+    return nnz * 8 + M * N * sz + R * N * sz + nnz * 4
 
 
 def step_bytes(M, nnz, R, N, sz):
-    spmm = (M + 1) * 8 + nnz * 8 + R * N * sz + M * N * 4
-    pack = 2 * R * N * sz + R * 4
-    return spmm, pack
+    return spmm_bytes(M, nnz, R, N, sz), pack_bytes(R, N, sz)
 
 
 def dist_env():
@@ -178,18 +230,67 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_from_profile():
-    """DRAM bytes per SpMM launch from the committed ncu summary, if the kernel is unchanged."""
+def sources_sha256() -> str:
+    h = hashlib.sha256()
+    for pat in KERNEL_SOURCE_GLOBS:
+        for f in sorted(glob.glob(os.path.join(ROOT, pat))):
+            h.update(os.path.relpath(f, ROOT).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def traffic_from_profile(kernel: str, workload_name_: str):
+    """DRAM bytes per launch of `kernel` on `workload_name_` from the committed ncu record, if
+    the library's sources are those the counters were taken on (else None)."""
     try:
-        rec = json.load(open(PROFILE_TRAFFIC))
+        recs = json.load(open(PROFILE_TRAFFIC))
     except (OSError, ValueError):
         return None
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    if rec.get("kernel_sources_sha256") != h.hexdigest():
-        return None
-    return rec.get("dram_bytes_per_launch")
+    sha = sources_sha256()
+    for r in recs.get("records", []):
+        if (r.get("kernel_name") == kernel and r.get("workload") == workload_name_
+                and r.get("sources_sha256") == sha):
+            return r.get("dram_bytes_per_launch")
+    return None
+
+
+def write_traffic_record(csv_path, instantiation, workload_name_, command):
+    """Adds (or replaces) the record of one kernel on one workload: the mean over the captured
+    launches of dram__bytes_read.sum + dram__bytes_write.sum, from an ncu raw CSV export."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    head = rows[0]
+    ci = {k: head.index(k) for k in ("Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum")}
+    units = rows[1] if len(rows) > 1 and not rows[1][ci["Kernel Name"]] else None
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    tot = []
+    name = instantiation.split("<")[0]
+    for r in rows[1 + (units is not None):]:
+        if not r[ci["Kernel Name"]].startswith(name):
+            continue
+        b = 0.0
+        for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            u = units[ci[k]] if units else "byte"
+            b += float(r[ci[k]].replace(",", "")) * scale.get(u, 1)
+        tot.append(b)
+    if not tot:
+        raise SystemExit(f"no launch of {name} in {csv_path}")
+    try:
+        recs = json.load(open(PROFILE_TRAFFIC))
+    except (OSError, ValueError):
+        recs = {"records": []}
+    recs["note"] = ("DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, ncu, "
+                    "--clock-control none), mean over the captured launches; valid while the "
+                    "library sources hash to sources_sha256")
+    recs["records"] = [r for r in recs.get("records", [])
+                       if not (r.get("kernel") == instantiation and r.get("workload") == workload_name_)]
+    recs["records"].append({"kernel": instantiation, "kernel_name": name, "workload": workload_name_,
+                            "dram_bytes_per_launch": int(round(sum(tot) / len(tot))),
+                            "launches": len(tot), "sources_sha256": sources_sha256(),
+                            "command": command})
+    with open(PROFILE_TRAFFIC, "w") as f:
+        json.dump(recs, f, indent=1)
+        f.write("\n")
 
 
 def cpu_model() -> str:
@@ -202,6 +303,16 @@ def cpu_model() -> str:
         if line.strip().lower().startswith("model name"):
             return line.split(":", 1)[1].strip()
     return ""
+
+
+def hbm_peak():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    if peaks.get("hbm_gbs"):
+        return float(peaks["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
 
 
 def cpu_baseline(A, B, args, stride=8):
@@ -221,12 +332,12 @@ def cpu_baseline(A, B, args, stride=8):
     Bp = oracle.pack(B, src)
     oracle.spmm_packed(S, P, Bp, B)
     t2 = time.perf_counter()
-    sp, pk = step_bytes(S.M, S.nnz, len(src), args.N, 4)
-    gbs = (sp + pk) / (t2 - t1) / 1e9
-    return {"value": gbs, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
-            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+    sp = spmm_bytes(S.M, S.nnz, len(src), args.N, 4)
+    return {"value": sp / (t2 - t1) / 1e9, "unit": "GB/s", "cores": oracle.threads(),
+            "kind": "oracle", "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "sample": f"every {stride}th row ({S.M} rows, {S.nnz} nnz), pack + SpMM via packed "
-                      f"rows in FP64; plan {t1 - t0:.2f} s not counted",
+                      f"rows in FP64 (SpMM bytes over pack + SpMM time); plan {t1 - t0:.2f} s "
+                      f"not counted",
             "seconds": t2 - t1}
 
 
@@ -254,11 +365,62 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded R-MAT)", "config": config(args, A),
+            "data": "synthetic (seeded R-MAT, counter-based SplitMix64)", "config": config(args, A),
             "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu_model", "nproc")},
             "e2e": {"value": res["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def timed(fn, stream, reps=20, warm=3):
+    """Mean device time of fn() in ms (CUDA events on `stream`, after `warm` untimed calls)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def gbps(nbytes, ms):
+    return nbytes / (ms * 1e-3) / 1e9
+
+
+def frac_entry(nbytes, ms, peak):
+    g = gbps(nbytes, ms)
+    return {"ms": ms, "bytes": int(nbytes), "GBps": g, "frac": g / peak}
+
+
+def measure_l2_ceiling(A, args, dev, stream, sz, tdt, reps):
+    """The same SpMM kernel, schedule and gather count with every packed row L2-resident: A's
+    columns are divided by a power of two so that the packed set is at most 32 MB (row structure,
+    nonzeros per row and their order unchanged; duplicates are summed), B is random."""
+    import torch
+    from paper_2512_20178_gb300 import shiro
+    N = args.N
+    row = N * sz
+    # Each row block's tiles together name at most K2 packed rows: K2 <= 32 MB / row / P_r.
+    target = max(args.tiles, (32 << 20) // row // args.tiles)
+    shift = max(0, int(np.ceil(np.log2(max(1.0, A.K / target)))))
+    K2 = ((A.K - 1) >> shift) + 1
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    colf = torch.from_numpy((A.col >> shift).astype(np.int32)).to(dev)
+    val = torch.from_numpy(A.val).to(dev)
+    P = shiro.Plan.create(rp, colf, val, A.M, K2, args.tiles, args.tiles)
+    R = P.info.packed_rows
+    Bp = torch.randn((R, N), device=dev).to(tdt)
+    C = torch.empty((A.M, N), dtype=torch.float32, device=dev)
+    scr = P.new_scratch(N, tdt)
+    ms = timed(lambda: P.spmm(Bp, out=C, scratch=scr), stream, reps)
+    gather_bytes = A.nnz * N * sz
+    return {"ms": ms, "packed_rows": R, "packed_MB": R * row / 1e6, "column_shift": shift,
+            "gather_bytes": gather_bytes, "gather_GBps": gbps(gather_bytes, ms),
+            "what": "same kernel and schedule, columns >> shift so the packed rows fit in L2"}
 
 
 def run_ours(args):
@@ -332,18 +494,84 @@ def run_ours(args):
     spmm_ms = sum(launch_ms) / K
     pct = lambda q: launch_ms[min(K - 1, int(q * (K - 1) + 0.5))]
     spmm_stats = {"mean": spmm_ms, "median": pct(0.5), "p10": pct(0.1), "p90": pct(0.9)}
+    pack_ms = ms - spmm_ms
     ms_max = reduce_max(ms, world, dev)
     sp_bytes, pk_bytes = step_bytes(A.M, A.nnz, R, N, sz)
-    value = world * (sp_bytes + pk_bytes) / (ms_max * 1e-3) / 1e9
+    value = world * sp_bytes / (ms_max * 1e-3) / 1e9
     gflops = world * 2.0 * A.nnz * N / (ms_max * 1e-3) / 1e9
+    peak, peak_src = hbm_peak()
+    wname = workload_name(args.scale, args.deg, N, args.tiles, args.dtype)
 
-    # End to end through the public API: every step copies its B from pinned host memory and
-    # reads its C back into pinned host memory.  Steps are pipelined as a serving loop would run
-    # them: step k+1's upload and step k-1's download overlap step k's pack + SpMM (two device
-    # buffers each for B and C, one stream per direction).  The serial figure (one stream, no
-    # overlap) is reported beside it.
+    ceiling = measure_l2_ceiling(A, args, dev, stream, sz, tdt, reps=max(10, min(K, 50)))
+    achieved = gbps(sp_bytes, spmm_ms)
+    kname = spmm_kernel(N, sz)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile(kname, wname), "algorithmic_bytes": sp_bytes,
+                "ms_per_launch": spmm_ms, "launch_ms": spmm_stats,
+                "ceilings": {
+                    "hbm_ms": sp_bytes / (peak * 1e9) * 1e3,
+                    "l2_gather_ms": ceiling["ms"],
+                    "l2_gather_frac": gbps(sp_bytes, ceiling["ms"]) / peak,
+                    "kernel_vs_l2_gather": ceiling["ms"] / spmm_ms,
+                    "l2_gather": ceiling}}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, P, Bh, Bd, Bp, C, scratch, stream, dev, sp_bytes, sz, world, K)
+
+    forms = None
+    fset = forms_of(args)
+    if fset and rank == 0:
+        fclocks = ClockSampler(dev.index if dev.index is not None else 0)
+        fclocks.start()
+        forms = measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream,
+                              peak, bf16)
+        fclocks.stop()
+        forms["clocks"] = fclocks.summary()
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": args.dtype,
+            "data": "synthetic (seeded R-MAT, counter-based SplitMix64)",
+            "config": config(args, A),
+            "value_definition": "SpMM algorithmic bytes / (pack + SpMM) step time",
+            "plan": {"packed_rows": R, "plan_ms": plan_ms, "schedule": P.info.opts.as_dict(),
+                     "autotuned": tuned},
+            "gflops": gflops, "spmm_ms": spmm_ms, "pack_ms": pack_ms,
+            "spmm_over_packed_GBps": achieved,
+            "pack_GBps": gbps(pk_bytes, pack_ms) if pack_ms > 0 else None,
+            "pack_bytes": pk_bytes,
+            "gpu_launches": 2 * K, "roofline": roofline, "clocks": clocks.summary()}
+    if e2e:
+        line["e2e"] = e2e
+    if forms:
+        line["forms"] = forms
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(A, B, args).items() if k != "seconds"}
+        cores = oracle.threads()
+        oracle.set_threads(1)
+        one = cpu_baseline(A, B, args, stride=128)
+        oracle.set_threads(cores)
+        line["cpu_baseline"]["one_thread"] = {"value": one["value"], "unit": "GB/s", "cores": 1,
+                                              "sample": one["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(args, P, Bh, Bd, Bp, C, scratch, stream, dev, sp_bytes, sz, world, K):
+    """End to end through the public API: every step copies its B from pinned host memory and
+    reads its C back into pinned host memory.  Steps are pipelined as a serving loop would run
+    them: step k+1's upload and step k-1's download overlap step k's pack + SpMM (two device
+    buffers each for B and C, one stream per direction).  The serial figure (one stream, no
+    overlap) is reported beside it."""
+    import torch
+    N = args.N
     Bh = Bh.pin_memory()
-    Ch = [torch.empty((A.M, N), dtype=torch.float32).pin_memory() for _ in range(2)]
+    Ch = [torch.empty(tuple(C.shape), dtype=torch.float32).pin_memory() for _ in range(2)]
     Bdd = [Bd, torch.empty_like(Bd)]
     Cd = [C, torch.empty_like(C)]
     s_up, s_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -385,156 +613,229 @@ def run_ours(args):
     # Serial: upload, step and download on one stream.
     for _ in range(2):
         Bd.copy_(Bh, non_blocking=True)
-        step()
+        P.pack(Bd, out=Bp)
+        P.spmm(Bp, out=C, scratch=scratch)
         Ch[0].copy_(C, non_blocking=True)
     torch.cuda.synchronize()
     e0.record(stream)
     Ks = max(1, min(K, 30))
     for _ in range(Ks):
         Bd.copy_(Bh, non_blocking=True)
-        step()
+        P.pack(Bd, out=Bp)
+        P.spmm(Bp, out=C, scratch=scratch)
         Ch[0].copy_(C, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     serial_ms = reduce_max(e0.elapsed_time(e1) / Ks, world, dev)
-    e2e = {"value": world * (sp_bytes + pk_bytes) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": int(Bh.numel() * sz), "d2h_bytes_per_step": int(Ch[0].numel() * 4),
-           "ms_per_step": e2e_ms, "pipelined": "upload k+1 / compute k / download k-1",
-           "serial_ms_per_step": serial_ms}
-    del Bdd, Cd
-
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
-    achieved = sp_bytes / (spmm_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": spmm_kernel(args.N, sz), "achieved": achieved, "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(), "algorithmic_bytes": sp_bytes,
-                "ms_per_launch": spmm_ms, "launch_ms": spmm_stats}
-
-    forms = None
-    if not args.no_forms and not bf16:
-        forms = measure_forms(args, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream)
-
-    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "storage": args.dtype,
-            "data": "synthetic (seeded R-MAT, counter-based SplitMix64)",
-            "config": config(args, A, {"packed_rows": R, "plan_ms": plan_ms,
-                                       "schedule": P.info.opts.as_dict(), "autotuned": tuned}),
-            "gflops": gflops, "spmm_ms": spmm_ms, "pack_ms": ms - spmm_ms,
-            "gpu_launches": 2 * K, "roofline": roofline, "e2e": e2e,
-            "clocks": clocks.summary()}
-    if forms:
-        line["forms"] = forms
-    if rank == 0 and world == 1 and not args.no_cpu:
-        import oracle
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(A, B, args).items() if k != "seconds"}
-        cores = oracle.threads()
-        oracle.set_threads(1)
-        one = cpu_baseline(A, B, args, stride=128)
-        oracle.set_threads(cores)
-        line["cpu_baseline"]["one_thread"] = {"value": one["value"], "unit": "GB/s", "cores": 1,
-                                              "sample": one["sample"]}
-    if rank == 0:
-        print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return {"value": world * gbps(sp_bytes, e2e_ms), "unit": "GB/s",
+            "h2d_bytes_per_step": int(Bh.numel() * sz), "d2h_bytes_per_step": int(Ch[0].numel() * 4),
+            "ms_per_step": e2e_ms, "pipelined": "upload k+1 / compute k / download k-1",
+            "serial_ms_per_step": serial_ms}
 
 
-def measure_forms(args, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream, reps=20):
-    """BF16-stored B, backward (dB and dA) and fwd+bwd on the same A, N (device times)."""
+def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, stream, peak,
+                  bf16, reps=20):
+    """Every other configuration on this GPU (device times, algorithmic bytes, frac of peak)."""
     import torch
     from paper_2512_20178_gb300 import shiro, synth
     N = args.N
-
-    def timed(fn):
-        for _ in range(3):
-            fn()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
     R = P.info.packed_rows
-    Bh16 = torch.from_numpy(synth.to_bf16_bits(B).view(np.int16)).to(dev).view(torch.bfloat16)
-    Bp16 = torch.empty((R, N), dtype=torch.bfloat16, device=dev)
-    s16 = P.new_scratch(N, torch.bfloat16)
-    bf16_ms = timed(lambda: (P.pack(Bh16, out=Bp16), P.spmm(Bp16, out=C, scratch=s16)))
-    sp16, pk16 = step_bytes(A.M, A.nnz, R, N, 2)
-    fwd_ms = timed(lambda: (P.pack(Bd, out=Bp), P.spmm(Bp, out=C, scratch=scratch)))
-    PT = shiro.Plan.create(rp, col, val, A.M, A.K, args.tiles, args.tiles,
-                           flags=shiro.SHIRO_PLAN_TRANSPOSE)
-    G = torch.randn((A.M, N), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
-    RT = PT.info.packed_rows
-    Gp = torch.empty((RT, N), dtype=torch.float32, device=dev)
-    dB = torch.empty((A.K, N), dtype=torch.float32, device=dev)
-    dA = torch.empty(A.nnz, dtype=torch.float32, device=dev)
-    sT = PT.new_scratch(N, torch.float32)
-    db_ms = timed(lambda: (PT.pack(G, out=Gp), PT.spmm(Gp, out=dB, scratch=sT)))
-    da_ms = timed(lambda: P.sddmm(G, Bp, out=dA))
-    sddmm_bytes = A.nnz * 8 + A.M * N * 4 + R * N * 4 + A.nnz * 4
-    # N sweep (FP32 B): pack + SpMM and SpMM alone at N = 32 .. 256 on the same plan.
-    n_sweep = {}
-    for n in (32, 64, 128, 256):
-        Bn = torch.from_numpy(synth.dense_normal(A.K, n, 7)).to(dev)
-        Bpn = torch.empty((R, n), dtype=torch.float32, device=dev)
-        Cn = torch.empty((A.M, n), dtype=torch.float32, device=dev)
-        sn = P.new_scratch(n, torch.float32)
-        P.pack(Bn, out=Bpn)
-        spmm_n = timed(lambda: P.spmm(Bpn, out=Cn, scratch=sn))
-        step_n = timed(lambda: (P.pack(Bn, out=Bpn), P.spmm(Bpn, out=Cn, scratch=sn)))
-        spb, pkb = step_bytes(A.M, A.nnz, R, n, 4)
-        n_sweep[str(n)] = {"spmm_ms": spmm_n, "step_ms": step_n,
-                           "spmm_GBps": spb / (spmm_n * 1e-3) / 1e9,
-                           "step_GBps": (spb + pkb) / (step_n * 1e-3) / 1e9}
-        del Bn, Bpn, Cn, sn
-    # Comparator (not on the path): cuSPARSE CSR SpMM through torch.sparse.mm on the unpacked B.
-    cus = None
-    try:
-        At = torch.sparse_csr_tensor(rp.to(torch.int32), col, val, size=(A.M, A.K))
-        Cc = torch.sparse.mm(At, Bd)
-        cus_ms = timed(lambda: torch.sparse.mm(At, Bd))
-        P.pack(Bd, out=Bp)
-        P.spmm(Bp, out=C, scratch=scratch)
-        torch.cuda.synchronize()
-        cus = {"ms": cus_ms, "ours_spmm_ms": timed(lambda: P.spmm(Bp, out=C, scratch=scratch)),
-               "ours_step_ms": fwd_ms, "max_abs_diff": float((Cc - C).abs().max()),
-               "what": "torch.sparse.mm (cuSPARSE CSR SpMM) on the original B, same A, N"}
-        del At, Cc
-    except Exception as e:  # the comparator is optional context
-        cus = {"unavailable": str(e).splitlines()[0][:200]}
-    return {"n_sweep_fp32": n_sweep, "cusparse": cus,"bf16_B": {"ms": bf16_ms, "GBps": (sp16 + pk16) / (bf16_ms * 1e-3) / 1e9,
-                       "vs_fp32_speedup": fwd_ms / bf16_ms},
-            "fp32_fwd_ms": fwd_ms, "bwd_dB_ms": db_ms, "bwd_dA_ms": da_ms,
-            "fwd_bwd_ms": fwd_ms + db_ms + da_ms,
-            "sddmm_GBps": sddmm_bytes / (da_ms * 1e-3) / 1e9,
-            "transpose_packed_rows": RT}
+    out = {"peak_GBps": peak}
+    run = lambda fn: timed(fn, stream, reps)
+    fwd_ms = run(lambda: (P.pack(Bd, out=Bp), P.spmm(Bp, out=C, scratch=scratch)))
+    if "backward" in fset and not bf16:
+        PT = shiro.Plan.create(rp, col, val, A.M, A.K, args.tiles, args.tiles,
+                               flags=shiro.SHIRO_PLAN_TRANSPOSE)
+        G = torch.randn((A.M, N), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+        RT = PT.info.packed_rows
+        Gp = torch.empty((RT, N), dtype=torch.float32, device=dev)
+        dB = torch.empty((A.K, N), dtype=torch.float32, device=dev)
+        dA = torch.empty(A.nnz, dtype=torch.float32, device=dev)
+        sT = PT.new_scratch(N, torch.float32)
+        PT.pack(G, out=Gp)
+        db_spmm = run(lambda: PT.spmm(Gp, out=dB, scratch=sT))
+        db_pack = run(lambda: PT.pack(G, out=Gp))
+        db_ms = run(lambda: (PT.pack(G, out=Gp), PT.spmm(Gp, out=dB, scratch=sT)))
+        da_ms = run(lambda: P.sddmm(G, Bp, out=dA))
+        wname = workload_name(args.scale, args.deg, N, args.tiles, "f32")
+        sd = frac_entry(sddmm_bytes(A.M, A.nnz, R, N, 4), da_ms, peak)
+        sd["kernel"] = "k_sddmm_lean"
+        sd["traffic"] = traffic_from_profile("k_sddmm_lean", wname)
+        out["backward"] = {
+            "workload": wname, "fwd_ms": fwd_ms, "fwd_bwd_ms": fwd_ms + db_ms + da_ms,
+            "dB_step_ms": db_ms, "dB_spmm": frac_entry(spmm_bytes(A.K, A.nnz, RT, N, 4), db_spmm, peak),
+            "dB_pack": frac_entry(pack_bytes(RT, N, 4), db_pack, peak),
+            "dB_step_GBps_spmm_bytes": gbps(spmm_bytes(A.K, A.nnz, RT, N, 4), db_ms),
+            "dA_sddmm": sd, "transpose_packed_rows": RT}
+        del PT, G, Gp, dB, dA, sT
+    if "bf16" in fset and not bf16:
+        Bh16 = torch.from_numpy(synth.to_bf16_bits(B).view(np.int16)).to(dev).view(torch.bfloat16)
+        Bp16 = torch.empty((R, N), dtype=torch.bfloat16, device=dev)
+        s16 = P.new_scratch(N, torch.bfloat16)
+        P.pack(Bh16, out=Bp16)
+        sp16 = run(lambda: P.spmm(Bp16, out=C, scratch=s16))
+        st16 = run(lambda: (P.pack(Bh16, out=Bp16), P.spmm(Bp16, out=C, scratch=s16)))
+        e = frac_entry(spmm_bytes(A.M, A.nnz, R, N, 2), sp16, peak)
+        out["bf16_B"] = {"spmm": e, "step_ms": st16,
+                         "step_GBps_spmm_bytes": gbps(spmm_bytes(A.M, A.nnz, R, N, 2), st16),
+                         "vs_fp32_step_speedup": fwd_ms / st16}
+        del Bh16, Bp16, s16
+    if "nsweep" in fset:
+        n_sweep = {}
+        for n in (32, 64, 128, 256):
+            Bn = torch.from_numpy(synth.dense_normal(A.K, n, 7)).to(dev)
+            Bpn = torch.empty((R, n), dtype=torch.float32, device=dev)
+            Cn = torch.empty((A.M, n), dtype=torch.float32, device=dev)
+            sn = P.new_scratch(n, torch.float32)
+            P.pack(Bn, out=Bpn)
+            spmm_n = run(lambda: P.spmm(Bpn, out=Cn, scratch=sn))
+            step_n = run(lambda: (P.pack(Bn, out=Bpn), P.spmm(Bpn, out=Cn, scratch=sn)))
+            e = frac_entry(spmm_bytes(A.M, A.nnz, R, n, 4), spmm_n, peak)
+            e["step_ms"] = step_n
+            e["step_GBps_spmm_bytes"] = gbps(spmm_bytes(A.M, A.nnz, R, n, 4), step_n)
+            n_sweep[str(n)] = e
+            del Bn, Bpn, Cn, sn
+        out["n_sweep_fp32"] = n_sweep
+    if "cusparse" in fset and not bf16:
+        # Comparator (not on the path): cuSPARSE CSR SpMM through torch.sparse.mm, unpacked B.
+        try:
+            At = torch.sparse_csr_tensor(rp.to(torch.int32), col, val, size=(A.M, A.K))
+            Cc = torch.sparse.mm(At, Bd)
+            cus_ms = run(lambda: torch.sparse.mm(At, Bd))
+            P.pack(Bd, out=Bp)
+            P.spmm(Bp, out=C, scratch=scratch)
+            torch.cuda.synchronize()
+            out["cusparse"] = {"ms": cus_ms, "ours_spmm_ms": run(lambda: P.spmm(Bp, out=C, scratch=scratch)),
+                               "ours_step_ms": fwd_ms, "max_abs_diff": float((Cc - C).abs().max()),
+                               "what": "torch.sparse.mm (cuSPARSE CSR SpMM) on the original B, same A, N"}
+            del At, Cc
+        except Exception as e:  # the comparator is optional context
+            out["cusparse"] = {"unavailable": str(e).splitlines()[0][:200]}
+    torch.cuda.empty_cache()
+    if "precision" in fset:
+        out["precision"] = form_precision(dev, stream, peak, reps)
+        torch.cuda.empty_cache()
+    if "gcn" in fset:
+        out["gcn"] = form_gcn(dev, stream, peak, reps)
+        torch.cuda.empty_cache()
+    if "batch" in fset:
+        out["batch"] = form_batch(dev, stream, peak, reps)
+        torch.cuda.empty_cache()
+    if "er" in fset:
+        out["er"] = form_er(dev, stream, peak, max(reps, 100))
+    return out
 
 
-def run_batch(args):
-    """Batched form: G graphs as one block-diagonal plan; each step replays one CUDA graph that
-    holds the pack and one persistent SpMM launch over every graph."""
+def form_precision(dev, stream, peak, reps, scale=22, deg=32, N=256, seed=3):
+    """The precision workload: R-MAT 2^22, avg degree 32, B 2^22 x 256 stored in BF16, FP32
+    accumulation and C, 4x4 tiles (the same matrix and B as its parity test)."""
     import torch
-    import __graft_entry__ as g
-    g.build()
     from paper_2512_20178_gb300 import shiro, synth
-    dev = torch.device("cuda", torch.cuda.current_device())
-    N = args.N
-    gb = synth.batch_graphs(args.batch, 5)
-    tens = []
-    for gr in gb.graphs:
-        tens.append((torch.from_numpy(gr.rowptr).to(dev), torch.from_numpy(gr.col).to(dev),
-                     torch.from_numpy(gr.val).to(dev), gr.M, gr.K))
+    A = synth.rmat(scale, deg, seed)
+    B = synth.dense_normal(A.K, N, seed)
+    Bd = torch.from_numpy(synth.to_bf16_bits(B).view(np.int16)).to(dev).view(torch.bfloat16)
+    del B
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    col = torch.from_numpy(A.col).to(dev)
+    val = torch.from_numpy(A.val).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P = shiro.Plan.create(rp, col, val, A.M, A.K, 4, 4)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    R = P.info.packed_rows
+    Bp = torch.empty((R, N), dtype=torch.bfloat16, device=dev)
+    C = torch.empty((A.M, N), dtype=torch.float32, device=dev)
+    scr = P.new_scratch(N, torch.bfloat16)
+    P.pack(Bd, out=Bp)
+    sp_ms = timed(lambda: P.spmm(Bp, out=C, scratch=scr), stream, reps)
+    pk_ms = timed(lambda: P.pack(Bd, out=Bp), stream, reps)
+    st_ms = timed(lambda: (P.pack(Bd, out=Bp), P.spmm(Bp, out=C, scratch=scr)), stream, reps)
+    spb = spmm_bytes(A.M, A.nnz, R, N, 2)
+    wname = workload_name(scale, deg, N, 4, "bf16")
+    e = frac_entry(spb, sp_ms, peak)
+    e["kernel"] = spmm_kernel(N, 2)
+    e["traffic"] = traffic_from_profile(spmm_kernel(N, 2), wname)
+    return {"workload": wname, "seed": seed, "M": A.M, "nnz": A.nnz, "packed_rows": R,
+            "plan_ms": plan_ms, "spmm": e, "pack": frac_entry(pack_bytes(R, N, 2), pk_ms, peak),
+            "step_ms": st_ms, "step_GBps_spmm_bytes": gbps(spb, st_ms),
+            "gather_bytes": A.nnz * N * 2, "gather_GBps": gbps(A.nnz * N * 2, sp_ms),
+            "gflops": 2.0 * A.nnz * N / (st_ms * 1e-3) / 1e9}
+
+
+def form_gcn(dev, stream, peak, reps, scale=20, deg=16, N=128, F=256, seed=4, tiles=4):
+    """GCN layer Y = A_hat (X W) through the public autograd wrapper: the dense product X W is
+    torch's (glue, timed on its own), A_hat times it is the library's pack + SpMM, and the backward
+    gives dX and dW through torch and dH (A_hat^T dY: pack + SpMM on the transposed plan) and the
+    gradient of A_hat's values (SDDMM) through the library.  Loss <G, Y> with a fixed G."""
+    import torch
+    from paper_2512_20178_gb300 import autograd, synth
+    A = synth.gcn_normalized(scale, deg, seed)
+    rp = torch.from_numpy(A.rowptr).to(dev)
+    col = torch.from_numpy(A.col).to(dev)
+    val = torch.from_numpy(A.val).to(dev).requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = autograd.SparseMatrix(rp, col, val, A.M, A.K, tiles, tiles)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    X = torch.from_numpy(synth.dense_normal(A.M, F, seed, std=0.02)).to(dev).requires_grad_(True)
+    W = torch.from_numpy(synth.dense_normal(F, N, seed + 1, std=0.02)).to(dev).requires_grad_(True)
+    G = torch.from_numpy(synth.dense_normal(A.M, N, seed + 2)).to(dev)
+
+    def fwd():
+        return autograd.spmm(S, torch.matmul(X, W))
+
+    def fwd_bwd():
+        X.grad = W.grad = val.grad = None
+        fwd().backward(G)
+
+    P, PT = S.plan, S.planT
+    R, RT = P.info.packed_rows, PT.info.packed_rows
+    with torch.no_grad():
+        H = torch.matmul(X, W)
+        glue_ms = timed(lambda: torch.matmul(X, W, out=H), stream, reps)
+        Hp = torch.empty((R, N), device=dev)
+        Y = torch.empty((A.M, N), device=dev)
+        sc = P.new_scratch(N, torch.float32)
+        P.pack(H, out=Hp)
+        spmm_ms = timed(lambda: P.spmm(Hp, out=Y, scratch=sc), stream, reps)
+        pack_ms = timed(lambda: P.pack(H, out=Hp), stream, reps)
+        Gp = torch.empty((RT, N), device=dev)
+        dH = torch.empty((A.K, N), device=dev)
+        scT = PT.new_scratch(N, torch.float32)
+        PT.pack(G, out=Gp)
+        dh_spmm = timed(lambda: PT.spmm(Gp, out=dH, scratch=scT), stream, reps)
+        dh_pack = timed(lambda: PT.pack(G, out=Gp), stream, reps)
+        dA = torch.empty(A.nnz, device=dev)
+        da_ms = timed(lambda: P.sddmm(G, Hp, out=dA), stream, reps)
+    fwd_ms = timed(fwd, stream, reps)
+    ms = timed(fwd_bwd, stream, reps)
+    return {"workload": f"gcn_rmat{scale}_deg{deg}_F{F}_N{N}_{tiles}x{tiles}_f32", "M": A.M,
+            "nnz": A.nnz, "F": F, "N": N, "plan_ms": plan_ms, "packed_rows": R,
+            "packed_rows_transpose": RT, "fwd_bwd_ms": ms, "fwd_ms": fwd_ms,
+            "dense_xw_ms": glue_ms,
+            "sparse_fwd": {"spmm": frac_entry(spmm_bytes(A.M, A.nnz, R, N, 4), spmm_ms, peak),
+                           "pack": frac_entry(pack_bytes(R, N, 4), pack_ms, peak)},
+            "sparse_bwd": {"dH_spmm": frac_entry(spmm_bytes(A.K, A.nnz, RT, N, 4), dh_spmm, peak),
+                           "dH_pack": frac_entry(pack_bytes(RT, N, 4), dh_pack, peak),
+                           "dA_sddmm": frac_entry(sddmm_bytes(A.M, A.nnz, R, N, 4), da_ms, peak)},
+            "sparse_ms": spmm_ms + pack_ms + dh_spmm + dh_pack + da_ms,
+            "sparse_fwd_gflops": 2.0 * A.nnz * N / (spmm_ms * 1e-3) / 1e9,
+            "what": "fwd + bwd through torch.autograd: X W and the dense gradients in torch (FP32), "
+                    "pack + SpMM, dH and dA_hat in the library"}
+
+
+def form_batch(dev, stream, peak, reps, G=512, N=64, seed=5):
+    """Batched form: G graphs as one block-diagonal plan; each step replays one CUDA graph that
+    holds the pack and one persistent SpMM launch over every graph.  Timed with the default
+    schedule and with the schedule the autotuner picks for this batch and N."""
+    import torch
+    from paper_2512_20178_gb300 import shiro, synth
+    gb = synth.batch_graphs(G, seed)
+    tens = [(torch.from_numpy(gr.rowptr).to(dev), torch.from_numpy(gr.col).to(dev),
+             torch.from_numpy(gr.val).to(dev), gr.M, gr.K) for gr in gb.graphs]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     P = shiro.Plan.create_batch(tens, opts=shiro.make_opts(persistent=1))
     torch.cuda.synchronize()
@@ -544,57 +845,50 @@ def run_batch(args):
     Bd = torch.from_numpy(synth.to_bf16_bits(Bh).view(np.int16)).to(dev).view(torch.bfloat16)
     Bp = torch.empty((R, N), dtype=torch.bfloat16, device=dev)
     C = torch.empty((M, N), dtype=torch.float32, device=dev)
-    # Autotuned schedule (group size, chunk size, CTA size, pipeline) for this batch and N.
+    spb = spmm_bytes(M, nnz, R, N, 2)
+
+    def graph_ms():
+        scratch = P.new_scratch(N, torch.bfloat16)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                P.pack(Bd, out=Bp)
+                P.spmm(Bp, out=C, scratch=scratch)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            P.pack(Bd, out=Bp)
+            P.spmm(Bp, out=C, scratch=scratch)
+        ms = timed(graph.replay, stream, reps)
+        del graph
+        return ms
+
+    default_opts = P.info.opts.as_dict()
+    default_ms = graph_ms()
     P.pack(Bd, out=Bp)
     tune_scr = torch.empty(64 << 20, dtype=torch.uint8, device=dev)
     tuned = P.autotune(Bp, C=C, scratch=tune_scr, reps=3)
     del tune_scr
-    scratch = P.new_scratch(N, torch.bfloat16)
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for _ in range(3):
-            P.pack(Bd, out=Bp)
-            P.spmm(Bp, out=C, scratch=scratch)
-    torch.cuda.current_stream().wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        P.pack(Bd, out=Bp)
-        P.spmm(Bp, out=C, scratch=scratch)
-    for _ in range(args.warmup):
-        graph.replay()
-    stream = torch.cuda.current_stream()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(args.steps):
-        graph.replay()
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.steps
-    sp, pk = step_bytes(M, nnz, R, N, 2)
-    print(json.dumps({
-        "metric": METRIC, "value": (sp + pk) / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "bf16",
-        "data": "synthetic (seeded R-MAT graphs)",
-        "config": {"workload": f"batch{args.batch}_rmat_n100-20000_deg4-40_N{N}_bf16_cudagraph",
-                   "graphs": args.batch, "rows": M, "nnz": nnz, "packed_rows": R, "N": N,
-                   "plan_ms": plan_ms, "schedule": P.info.opts.as_dict(), "autotuned": True},
-        "gflops": 2.0 * nnz * N / (ms * 1e-3) / 1e9, "gpu_launches": 2 * args.steps}))
+    tuned_ms = graph_ms()
+    e = frac_entry(spb, tuned_ms, peak)
+    e["bytes_note"] = "SpMM bytes over the pack + SpMM graph replay"
+    return {"workload": f"batch{G}_rmat_n100-20000_deg4-40_N{N}_bf16_cudagraph", "graphs": G,
+            "rows": M, "nnz": nnz, "packed_rows": R, "plan_ms": plan_ms,
+            "default": {"schedule": default_opts, "ms": default_ms,
+                        "GBps": gbps(spb, default_ms), "frac": gbps(spb, default_ms) / peak},
+            "tuned": {"schedule": tuned, **e}, "tuned_speedup": default_ms / tuned_ms,
+            "gflops": 2.0 * nnz * N / (tuned_ms * 1e-3) / 1e9}
 
 
-def run_er(args):
+def form_er(dev, stream, peak, reps, n=4096, N=32, P_=4, seed=1):
     """The small 1D configuration: ER G(4096, 8/4096), N = 32, P = 4 row blocks whose diagonal
-    tiles read B in place (LOCAL_DIAG) and whose off-diagonal tiles are packed."""
+    tiles read B in place (LOCAL_DIAG) and whose off-diagonal tiles are packed (L2-resident and
+    launch-bound: reported, not roofline-judged)."""
     import torch
-    import __graft_entry__ as g
-    g.build()
     from paper_2512_20178_gb300 import shiro, synth
-    dev = torch.device("cuda", torch.cuda.current_device())
-    n, N, P_ = 4096, 32, 4
-    A = synth.er(n, 8, 1)
-    Bd = torch.from_numpy(synth.dense_normal(n, N, 1)).to(dev)
+    A = synth.er(n, 8, seed)
+    Bd = torch.from_numpy(synth.dense_normal(n, N, seed)).to(dev)
     rp = torch.from_numpy(A.rowptr).to(dev)
     col = torch.from_numpy(A.col).to(dev)
     val = torch.from_numpy(A.val).to(dev)
@@ -603,111 +897,60 @@ def run_er(args):
     Bp = torch.empty((max(R, 1), N), dtype=torch.float32, device=dev)
     C = torch.empty((A.M, N), dtype=torch.float32, device=dev)
     scratch = P.new_scratch(N, torch.float32)
-    stream = torch.cuda.current_stream()
-    for _ in range(max(args.warmup, 3)):
-        P.pack(Bd, out=Bp)
-        P.spmm(Bp, B=Bd, out=C, scratch=scratch)
-    K = max(args.steps, 100)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(K):
-        P.pack(Bd, out=Bp)
-        P.spmm(Bp, B=Bd, out=C, scratch=scratch)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / K
-    # Bytes: SpMM reads the packed rows of off-diagonal tiles and, in place, the B rows named by
-    # the diagonal tiles' Cols.
+    ms = timed(lambda: (P.pack(Bd, out=Bp), P.spmm(Bp, B=Bd, out=C, scratch=scratch)), stream, reps)
+    # SpMM reads the packed rows of off-diagonal tiles and, in place, the B rows named by the
+    # diagonal tiles' Cols.
     ncols = P.tile_stats()["tile_ncols"].numpy()
     diag_cols = int(sum(ncols[p * P_ + p] for p in range(P_)))
-    sp, pk = step_bytes(A.M, A.nnz, R + diag_cols, N, 4)
-    pk = 2 * R * N * 4 + R * 4
-    print(json.dumps({
-        "metric": METRIC, "value": (sp + pk) / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
-        "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "f32",
-        "data": "synthetic (seeded Erdos-Renyi)",
-        "config": {"workload": "er4096_deg8_N32_1d_p4_local_diag", "M": A.M, "nnz": A.nnz,
-                   "N": N, "packed_rows_offdiag": R, "diag_cols": diag_cols,
-                   "l2": "L2-resident (launch-bound)"},
-        "note": "two launches per step of a few microseconds each: reported, not roofline-judged",
-        "gpu_launches": 2 * K}))
+    e = frac_entry(spmm_bytes(A.M, A.nnz, R + diag_cols, N, 4), ms, peak)
+    e["note"] = "two launches of a few microseconds: L2-resident, launch-bound, not roofline-judged"
+    return {"workload": "er4096_deg8_N32_1d_p4_local_diag", "M": A.M, "nnz": A.nnz,
+            "packed_rows_offdiag": R, "diag_cols": diag_cols, "step": e}
 
 
-def run_gcn(args):
-    """GCN layer Y = A_hat (X W) through the public autograd wrapper: the dense product X W is
-    torch's (glue, timed on its own), A_hat times it is the library's pack + SpMM, and the backward
-    gives dX and dW through torch and dH (A_hat^T dY: pack + SpMM on the transposed plan) and the
-    gradient of A_hat's values (SDDMM) through the library.  Loss <G, Y> with a fixed G."""
+def run_single_form(args, which):
+    """--gcn / --batch / --er: one JSON line for that configuration alone."""
     import torch
     import __graft_entry__ as g
     g.build()
-    from paper_2512_20178_gb300 import autograd, synth
     dev = torch.device("cuda", torch.cuda.current_device())
-    seed = 4
-    A = synth.gcn_normalized(args.scale, args.deg, seed)
-    F, N = 256, args.N
-    rp = torch.from_numpy(A.rowptr).to(dev)
-    col = torch.from_numpy(A.col).to(dev)
-    val = torch.from_numpy(A.val).to(dev).requires_grad_(True)
-    t0 = time.perf_counter()
-    S = autograd.SparseMatrix(rp, col, val, A.M, A.K, args.tiles, args.tiles)
-    torch.cuda.synchronize()
-    plan_ms = 1e3 * (time.perf_counter() - t0)
-    X = torch.from_numpy(synth.dense_normal(A.M, F, seed, std=0.02)).to(dev).requires_grad_(True)
-    W = torch.from_numpy(synth.dense_normal(F, N, seed + 1, std=0.02)).to(dev).requires_grad_(True)
-    G = torch.from_numpy(synth.dense_normal(A.M, N, seed + 2)).to(dev)
     stream = torch.cuda.current_stream()
-
-    def fwd():
-        return autograd.spmm(S, torch.matmul(X, W))
-
-    def fwd_bwd():
-        X.grad = W.grad = val.grad = None
-        fwd().backward(G)
-
-    def timed(fn, k):
-        for _ in range(args.warmup):
-            fn()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(k):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / k
-
-    with torch.no_grad():
-        H = torch.matmul(X, W)
-        glue_ms = timed(lambda: torch.matmul(X, W, out=H), args.steps)
-        sparse_fwd_ms = timed(lambda: autograd.spmm(S, H), args.steps)
-    fwd_ms = timed(fwd, args.steps)
-    ms = timed(fwd_bwd, args.steps)
-    print(json.dumps({
-        "metric": "GCN layer fwd+bwd ms", "value": ms, "unit": "ms", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "storage": "f32",
-        "data": "synthetic (seeded R-MAT, symmetrised, self loops, 1/sqrt(d_i d_j))",
-        "config": {"workload": f"gcn_rmat{args.scale}_deg{args.deg}_F{F}_N{N}_{args.tiles}x{args.tiles}",
-                   "M": A.M, "nnz": A.nnz, "F": F, "N": N, "plan_ms": plan_ms,
-                   "packed_rows": S.plan.info.packed_rows,
-                   "packed_rows_transpose": S.planT.info.packed_rows},
-        "fwd_ms": fwd_ms, "dense_xw_ms": glue_ms, "sparse_fwd_ms": sparse_fwd_ms,
-        "sparse_fwd_gflops": 2.0 * A.nnz * N / (sparse_fwd_ms * 1e-3) / 1e9}))
+    peak, _ = hbm_peak()
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    if which == "gcn":
+        r = form_gcn(dev, stream, peak, args.steps, scale=args.scale, deg=args.deg, N=args.N)
+        value, unit, hib, ms = r["fwd_bwd_ms"], "ms", False, r["fwd_bwd_ms"]
+    elif which == "batch":
+        r = form_batch(dev, stream, peak, args.steps, G=args.batch, N=args.N)
+        value, unit, hib, ms = r["tuned"]["GBps"], "GB/s", True, r["tuned"]["ms"]
+    else:
+        r = form_er(dev, stream, peak, max(args.steps, 100))
+        value, unit, hib, ms = r["step"]["GBps"], "GB/s", True, r["step"]["ms"]
+    clocks.stop()
+    print(json.dumps({"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1,
+                      "steps": args.steps, "warmup": 3, "ms_per_step": ms,
+                      "higher_is_better": hib, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f32", "data": "synthetic (seeded)",
+                      "config": {"workload": r["workload"]}, "detail": r,
+                      "clocks": clocks.summary()}))
 
 
 def main():
     args = parse()
+    if args.traffic_from:
+        if not (args.kernel and args.workload):
+            raise SystemExit("--traffic-from needs --kernel and --workload")
+        write_traffic_record(args.traffic_from, args.kernel, args.workload, args.command or "")
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.gcn:
-        run_gcn(args)
+        run_single_form(args, "gcn")
     elif args.er:
-        run_er(args)
+        run_single_form(args, "er")
     elif args.batch:
-        run_batch(args)
+        run_single_form(args, "batch")
     else:
         run_ours(args)
 

@@ -1,7 +1,6 @@
 """Host-side reporting logic of bench.py (CPU only): clock-sample parsing, the kernel name the
 roofline reports, and the rule that a stored DRAM-traffic figure is used only while the kernel
 sources it was measured on are unchanged."""
-import hashlib
 import json
 import os
 
@@ -39,17 +38,48 @@ def test_spmm_kernel_names():
 
 
 def test_traffic_record_follows_the_sources(tmp_path, monkeypatch):
-    h = hashlib.sha256()
-    for f in bench.KERNEL_SOURCES:
-        h.update(open(os.path.join(bench.ROOT, f), "rb").read())
     p = tmp_path / "traffic.json"
     monkeypatch.setattr(bench, "PROFILE_TRAFFIC", str(p))
-    # A record taken on the current sources is used ...
-    p.write_text(json.dumps({"kernel_sources_sha256": h.hexdigest(),
-                             "dram_bytes_per_launch": 123456}))
-    assert bench.traffic_from_profile() == 123456
+    rec = {"kernel": "k_spmm_lean_dyn<float, float, 4, 1, 4, false>",
+           "kernel_name": "k_spmm_lean_dyn", "workload": "rmat20_deg16_N128_4x4_f32",
+           "sources_sha256": bench.sources_sha256(), "dram_bytes_per_launch": 123456}
+    # A record taken on the current sources is used for its kernel and workload only ...
+    p.write_text(json.dumps({"records": [rec]}))
+    assert bench.traffic_from_profile("k_spmm_lean_dyn", "rmat20_deg16_N128_4x4_f32") == 123456
+    assert bench.traffic_from_profile("k_spmm_lean_dyn", "rmat22_deg32_N256_4x4_bf16") is None
+    assert bench.traffic_from_profile("k_sddmm_lean", "rmat20_deg16_N128_4x4_f32") is None
     # ... one taken on other sources is not, and neither is a missing record.
-    p.write_text(json.dumps({"kernel_sources_sha256": "0" * 64, "dram_bytes_per_launch": 1}))
-    assert bench.traffic_from_profile() is None
+    p.write_text(json.dumps({"records": [dict(rec, sources_sha256="0" * 64)]}))
+    assert bench.traffic_from_profile("k_spmm_lean_dyn", "rmat20_deg16_N128_4x4_f32") is None
     monkeypatch.setattr(bench, "PROFILE_TRAFFIC", str(tmp_path / "missing.json"))
-    assert bench.traffic_from_profile() is None
+    assert bench.traffic_from_profile("k_spmm_lean_dyn", "rmat20_deg16_N128_4x4_f32") is None
+
+
+def test_traffic_record_from_ncu_csv(tmp_path, monkeypatch):
+    """An ncu raw CSV export (a header row, a units row, one row per launch) becomes one record:
+    the mean over the launches of the named kernel of DRAM bytes read + written."""
+    monkeypatch.setattr(bench, "PROFILE_TRAFFIC", str(tmp_path / "traffic.json"))
+    csv = tmp_path / "raw.csv"
+    csv.write_text('"ID","Kernel Name","dram__bytes_read.sum","dram__bytes_write.sum"\n'
+                   '"","","Gbyte","Mbyte"\n'
+                   '"0","k_pack_rows<float>","1.5","10"\n'
+                   '"1","k_spmm_lean_dyn<float, float, 4, 1, 4, false>","1.0","500"\n'
+                   '"2","k_spmm_lean_dyn<float, float, 4, 1, 4, false>","2.0","700"\n')
+    bench.write_traffic_record(str(csv), "k_spmm_lean_dyn<float, float, 4, 1, 4, false>",
+                               "rmat20_deg16_N128_4x4_f32", "ncu ...")
+    r = json.load(open(tmp_path / "traffic.json"))["records"]
+    assert len(r) == 1 and r[0]["launches"] == 2
+    assert r[0]["dram_bytes_per_launch"] == int((1.0e9 + 0.5e9 + 2.0e9 + 0.7e9) / 2)
+    assert bench.traffic_from_profile("k_spmm_lean_dyn", "rmat20_deg16_N128_4x4_f32") == r[0]["dram_bytes_per_launch"]
+
+
+def test_l2_ceiling_fold_and_forms_parsing():
+    a = bench.parse(["--forms", "gcn,er"])
+    assert bench.forms_of(a) == {"gcn", "er"} and a.seed == 2
+    assert bench.forms_of(bench.parse(["--no-forms"])) == set()
+    assert bench.forms_of(bench.parse([])) == set(bench.FORMS)
+    assert bench.parse(["--scale", "22", "--deg", "32"]).seed == 3
+    # The algorithmic byte counts of the JSON line.
+    assert bench.spmm_bytes(10, 20, 5, 4, 2) == 11 * 8 + 20 * 8 + 5 * 4 * 2 + 10 * 4 * 4
+    assert bench.pack_bytes(5, 4, 2) == 2 * 5 * 4 * 2 + 5 * 4
+    assert bench.sddmm_bytes(10, 20, 5, 4, 4) == 20 * 8 + 10 * 4 * 4 + 5 * 4 * 4 + 20 * 4

@@ -218,12 +218,41 @@ __global__ void __launch_bounds__(256, (SddmmOcc<VEC, NCH, TB>::MIN_BLOCKS))
 }  // namespace shiro
 
 #include "sddmm_lean.cuh"
+#include "sddmm_group.cuh"
 
 namespace shiro {
 
 template <typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& prm,
                                  cudaStream_t s) {
+  // Lane groups (sddmm_group.cuh), the default for FP32 / BF16 rows of 128, 256 or 512 bytes with
+  // 16-byte aligned rows, outside persistent mode: eight lanes per nonzero, four nonzeros per warp
+  // step, items from a counter in the plan.
+  if constexpr (!MASKED && NCH == 1 && !std::is_same<TB, double>::value) {
+    constexpr int RB = 32 * VEC * (int)sizeof(TB);
+    if constexpr (RB == 128 || RB == 256 || RB == 512) {
+      auto al16 = [](const void* ptr, int64_t ld) {
+        return ((uintptr_t)ptr % 16) == 0 && ((uint64_t)ld * sizeof(TB)) % 16 == 0;
+      };
+      const bool ok16 = al16(prm.Bpack, prm.ldp) && al16(prm.dC, prm.lddc) &&
+                        (!(P->flags & SHIRO_PLAN_LOCAL_DIAG) || al16(prm.B, prm.ldb));
+      if (!prm.persistent && P->opts.pipeline == 0 && ok16) {
+        if (prm.n_items > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+        int per_sm = 0;
+        SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_sddmm_grp<TB, RB / 128>, 64, 0));
+        const int64_t grid = std::min<int64_t>((prm.n_items + 1) / 2,
+                                               (int64_t)std::max(per_sm, 1) * P->sm_count);
+        if (grid <= 0) return SHIRO_OK;
+        SddmmParams<TB> q = prm;
+        q.work = P->d_status + 2;
+        SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));
+        k_sddmm_grp<TB, RB / 128><<<(unsigned)grid, 64, 0, s>>>(q);
+        SHIRO_CUDA(cudaGetLastError());
+        return SHIRO_OK;
+      }
+    }
+  }
   // 48-register kernels outside persistent mode and pipeline 5: BF16 rows of 256 or 512 bytes and
   // FP32 rows of 256 bytes (N = 64) with the shared-memory tile reduction, FP32 rows of 512 bytes
   // (N = 128) with the 4-wide shuffle butterfly (the tile with pipeline 6).  Measured on R-MAT
@@ -234,9 +263,11 @@ static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& p
   if constexpr (!MASKED && NCH == 1 && !std::is_same<TB, double>::value &&
                 VEC * sizeof(TB) >= 8) {
     constexpr bool BF = std::is_same<TB, __nv_bfloat16>::value;
+    // Pipeline 3 (or 0 when the rows are not 16-byte aligned) takes the butterfly for FP32 rows
+    // of 512 bytes; pipeline 6 and the other rows take the tile.
     const bool tile = BF || VEC == 2 || P->opts.pipeline == 6;
     const bool shfl = !BF && VEC == 4 && P->opts.pipeline != 6;  // FP32 N = 128 rows
-    if (!prm.persistent && P->opts.pipeline != 5 && (tile || shfl)) {
+    if (!prm.persistent && P->opts.pipeline != 5 && (tile || shfl)) {  // pipelines 0, 3, 6
       int64_t grid = (prm.n_items + 1) / 2;
       if (grid <= 0) return SHIRO_OK;
       if (grid > INT32_MAX || prm.n_items > INT32_MAX)
@@ -376,9 +407,8 @@ shiro_status shiro_spmm_backward(shiro_plan_t plan, shiro_plan_t planT, const vo
       SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "dB needs the TRANSPOSE plan of the same matrix");
     if (planT->M != plan->K || planT->K != plan->M || planT->nnz != plan->nnz)
       SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "planT is not the transpose of plan");
-    SHIRO_TRY(launch_pack(planT, dC, lddc, N, dt, dCpack, lddp, s));
-    SHIRO_TRY(launch_spmm(planT, dCpack, lddp, dC, lddc, N, dt, dB, lddb, 0, scratch,
-                          scratch_bytes, s));
+    SHIRO_TRY(launch_pack_spmm(planT, dC, lddc, N, dt, dCpack, lddp, dB, lddb, 0, scratch,
+                               scratch_bytes, s));
   }
   if (dA) SHIRO_TRY(launch_sddmm(plan, dC, lddc, Bpack, ldp, B, ldb, N, dt, dA, s));
   return SHIRO_OK;

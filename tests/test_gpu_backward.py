@@ -171,9 +171,10 @@ def test_gcn_full_fp32_vs_oracle():
 @pytest.mark.parametrize("case", ["f32_n128", "f32_n64", "bf16_n128", "bf16_n256", "hub",
                                   "local_diag", "empty_rows", "ragged"])
 def test_sddmm_kernels(case):
-    """dA by every SDDMM kernel -- 48 registers with the shared-memory tile reduction (BF16 and
-    FP32 N = 64 default, pipeline 6 for FP32 N = 128), 48 registers with the 4-wide shuffle
-    butterfly (FP32 N = 128 default) and 64 registers with the 8-wide butterfly (pipeline 5,
+    """dA by every SDDMM kernel -- lane groups of eight lanes per nonzero (the default for 16-byte
+    aligned rows of 128 to 512 bytes), 48 registers with the shared-memory tile reduction
+    (pipeline 6; pipeline 3 for BF16 and FP32 N = 64), 48 registers with the 4-wide shuffle
+    butterfly (pipeline 3, FP32 N = 128) and 64 registers with the 8-wide butterfly (pipeline 5,
     persistent mode) -- within the oracle bound on the same inputs, including hub rows cut into
     chunks, 1D local diagonal tiles read from B in place, empty rows and a ragged last batch."""
     shiro = gu.lib()
@@ -202,7 +203,7 @@ def test_sddmm_kernels(case):
     Gd = torch.from_numpy(G).to(d).to(dt)
     ref = oracle.sddmm(A, G, B)
     scale = oracle.sddmm(A, np.abs(G), np.abs(B))
-    for pipe, pers in [(0, 0), (5, 0), (6, 0), (0, 1)]:
+    for pipe, pers in [(0, 0), (3, 0), (5, 0), (6, 0), (0, 1)]:
         opts = shiro.make_opts(pipeline=pipe, persistent=pers, long_row_nnz=128, chunk_nnz=64)
         P = gu.plan_of(A, 4, 4, flags, opts=opts)
         Bp = P.pack(Bd)

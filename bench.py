@@ -53,6 +53,12 @@ KERNEL_SOURCE_GLOBS = ["paper_2512_20178_gb300/csrc/*.cu", "paper_2512_20178_gb3
 FORMS = ("backward", "bf16", "nsweep", "cusparse", "precision", "gcn", "batch", "er")
 
 
+def fused_step(N, sz):
+    """Whether shiro_pack_spmm runs as one launch (k_spmm_lean_fused) with the default schedule:
+    rows of 512 bytes (FP32 N = 128, BF16 N = 256)."""
+    return N * sz == 512
+
+
 def spmm_kernel(N, sz):
     """The SpMM kernel the automatic pipeline picks for N columns of sz-byte elements."""
     row = N * sz
@@ -462,39 +468,34 @@ def run_ours(args):
         tuned = P.autotune(Bp, B=Bd, C=C)
     scratch = P.new_scratch(N, tdt)
     stream = torch.cuda.current_stream()
+    fused = fused_step(N, sz) and not args.autotune
 
     def step():
-        P.pack(Bd, out=Bp)
-        P.spmm(Bp, out=C, scratch=scratch)
+        # One step of the hot path through the public API: pack (stage 3) + SpMM (stage 5).
+        P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scratch)
 
     for _ in range(args.warmup):
         step()
     K = args.steps
-    ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     clocks = ClockSampler(dev.index if dev.index is not None else 0)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    start.record(stream)
+    ev[0].record(stream)
     for k in range(K):
-        P.pack(Bd, out=Bp)
-        ev_a[k].record(stream)
-        P.spmm(Bp, out=C, scratch=scratch)
-        ev_b[k].record(stream)
-    end.record(stream)
+        step()
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks.stop()
-    ms = start.elapsed_time(end) / K
-    launch_ms = sorted(a.elapsed_time(b) for a, b in zip(ev_a, ev_b))
-    spmm_ms = sum(launch_ms) / K
-    pct = lambda q: launch_ms[min(K - 1, int(q * (K - 1) + 0.5))]
-    spmm_stats = {"mean": spmm_ms, "median": pct(0.5), "p10": pct(0.1), "p90": pct(0.9)}
-    pack_ms = ms - spmm_ms
+    ms = ev[0].elapsed_time(ev[K]) / K
+    step_ms = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(K))
+    pct = lambda xs, q: xs[min(len(xs) - 1, int(q * (len(xs) - 1) + 0.5))]
+    step_stats = {"mean": ms, "median": pct(step_ms, 0.5), "p10": pct(step_ms, 0.1),
+                  "p90": pct(step_ms, 0.9)}
     ms_max = reduce_max(ms, world, dev)
     sp_bytes, pk_bytes = step_bytes(A.M, A.nnz, R, N, sz)
     value = world * sp_bytes / (ms_max * 1e-3) / 1e9
@@ -502,19 +503,51 @@ def run_ours(args):
     peak, peak_src = hbm_peak()
     wname = workload_name(args.scale, args.deg, N, args.tiles, args.dtype)
 
+    # The SpMM kernel alone over pre-packed rows (events around each launch) and the pack alone.
+    P.pack(Bd, out=Bp)
+    torch.cuda.synchronize()
+    Ks = max(10, min(K, 100))
+    ea = [torch.cuda.Event(enable_timing=True) for _ in range(Ks)]
+    eb = [torch.cuda.Event(enable_timing=True) for _ in range(Ks)]
+    for k in range(3):
+        P.spmm(Bp, out=C, scratch=scratch)
+    for k in range(Ks):
+        ea[k].record(stream)
+        P.spmm(Bp, out=C, scratch=scratch)
+        eb[k].record(stream)
+    torch.cuda.synchronize()
+    launch_ms = sorted(a.elapsed_time(b) for a, b in zip(ea, eb))
+    spmm_ms = sum(launch_ms) / Ks
+    spmm_stats = {"mean": spmm_ms, "median": pct(launch_ms, 0.5), "p10": pct(launch_ms, 0.1),
+                  "p90": pct(launch_ms, 0.9)}
+    pack_ms = timed(lambda: P.pack(Bd, out=Bp), stream, Ks)
+
     ceiling = measure_l2_ceiling(A, args, dev, stream, sz, tdt, reps=max(10, min(K, 50)))
-    achieved = gbps(sp_bytes, spmm_ms)
+    achieved_spmm = gbps(sp_bytes, spmm_ms)
     kname = spmm_kernel(N, sz)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(kname, wname), "algorithmic_bytes": sp_bytes,
-                "ms_per_launch": spmm_ms, "launch_ms": spmm_stats,
-                "ceilings": {
-                    "hbm_ms": sp_bytes / (peak * 1e9) * 1e3,
-                    "l2_gather_ms": ceiling["ms"],
-                    "l2_gather_frac": gbps(sp_bytes, ceiling["ms"]) / peak,
-                    "kernel_vs_l2_gather": ceiling["ms"] / spmm_ms,
-                    "l2_gather": ceiling}}
+    spmm_roof = {"bound": "hbm", "kernel": kname, "achieved": achieved_spmm, "peak": peak,
+                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved_spmm / peak,
+                 "traffic": traffic_from_profile(kname, wname), "algorithmic_bytes": sp_bytes,
+                 "ms_per_launch": spmm_ms, "launch_ms": spmm_stats,
+                 "ceilings": {
+                     "hbm_ms": sp_bytes / (peak * 1e9) * 1e3,
+                     "l2_gather_ms": ceiling["ms"],
+                     "l2_gather_frac": gbps(sp_bytes, ceiling["ms"]) / peak,
+                     "kernel_vs_l2_gather": ceiling["ms"] / spmm_ms,
+                     "l2_gather": ceiling}}
+    if fused:
+        # The step is one launch of the fused kernel: its algorithmic bytes are the pack's and
+        # the SpMM's, each counted once.
+        ach = gbps(sp_bytes + pk_bytes, ms)
+        roofline = {"bound": "hbm", "kernel": "k_spmm_lean_fused", "achieved": ach, "peak": peak,
+                    "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": traffic_from_profile("k_spmm_lean_fused", wname),
+                    "algorithmic_bytes": sp_bytes + pk_bytes,
+                    "bytes_definition": "pack 2*R*N*sz + R*4 plus SpMM (M+1)*8 + nnz*8 + R*N*sz + M*N*4",
+                    "ms_per_launch": ms, "launch_ms": step_stats,
+                    "spmm_kernel": spmm_roof}
+    else:
+        roofline = dict(spmm_roof)
 
     e2e = None
     if not args.no_e2e:
@@ -536,13 +569,16 @@ def run_ours(args):
             "data": "synthetic (seeded R-MAT, counter-based SplitMix64)",
             "config": config(args, A),
             "value_definition": "SpMM algorithmic bytes / (pack + SpMM) step time",
+            "step_ms": step_stats,
             "plan": {"packed_rows": R, "plan_ms": plan_ms, "schedule": P.info.opts.as_dict(),
                      "autotuned": tuned},
-            "gflops": gflops, "spmm_ms": spmm_ms, "pack_ms": pack_ms,
-            "spmm_over_packed_GBps": achieved,
-            "pack_GBps": gbps(pk_bytes, pack_ms) if pack_ms > 0 else None,
-            "pack_bytes": pk_bytes,
-            "gpu_launches": 2 * K, "roofline": roofline, "clocks": clocks.summary()}
+            "gflops": gflops, "step": "shiro_pack_spmm" + (" (one launch)" if fused else
+                                                            " (pack, then SpMM)"),
+            "spmm_ms": spmm_ms, "pack_ms": pack_ms, "two_launch_ms": spmm_ms + pack_ms,
+            "spmm_over_packed_GBps": achieved_spmm,
+            "pack_GBps": gbps(pk_bytes, pack_ms), "pack_bytes": pk_bytes,
+            "gpu_launches": (1 if fused else 2) * K, "roofline": roofline,
+            "clocks": clocks.summary()}
     if e2e:
         line["e2e"] = e2e
     if forms:
@@ -588,8 +624,7 @@ def measure_e2e(args, P, Bh, Bd, Bp, C, scratch, stream, dev, sp_bytes, sz, worl
             up_done[j].record(s_up)
         stream.wait_event(up_done[j])
         stream.wait_event(down_done[j])            # C buffer j read back
-        P.pack(Bdd[j], out=Bp)
-        P.spmm(Bp, out=Cd[j], scratch=scratch)
+        P.pack_spmm(Bdd[j], Bpack=Bp, out=Cd[j], scratch=scratch)
         comp_done[j].record(stream)
         with torch.cuda.stream(s_down):
             s_down.wait_event(comp_done[j])
@@ -613,16 +648,14 @@ def measure_e2e(args, P, Bh, Bd, Bp, C, scratch, stream, dev, sp_bytes, sz, worl
     # Serial: upload, step and download on one stream.
     for _ in range(2):
         Bd.copy_(Bh, non_blocking=True)
-        P.pack(Bd, out=Bp)
-        P.spmm(Bp, out=C, scratch=scratch)
+        P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scratch)
         Ch[0].copy_(C, non_blocking=True)
     torch.cuda.synchronize()
     e0.record(stream)
     Ks = max(1, min(K, 30))
     for _ in range(Ks):
         Bd.copy_(Bh, non_blocking=True)
-        P.pack(Bd, out=Bp)
-        P.spmm(Bp, out=C, scratch=scratch)
+        P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scratch)
         Ch[0].copy_(C, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -642,7 +675,7 @@ def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, st
     R = P.info.packed_rows
     out = {"peak_GBps": peak}
     run = lambda fn: timed(fn, stream, reps)
-    fwd_ms = run(lambda: (P.pack(Bd, out=Bp), P.spmm(Bp, out=C, scratch=scratch)))
+    fwd_ms = run(lambda: P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scratch))
     if "backward" in fset and not bf16:
         PT = shiro.Plan.create(rp, col, val, A.M, A.K, args.tiles, args.tiles,
                                flags=shiro.SHIRO_PLAN_TRANSPOSE)
@@ -655,12 +688,12 @@ def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, st
         PT.pack(G, out=Gp)
         db_spmm = run(lambda: PT.spmm(Gp, out=dB, scratch=sT))
         db_pack = run(lambda: PT.pack(G, out=Gp))
-        db_ms = run(lambda: (PT.pack(G, out=Gp), PT.spmm(Gp, out=dB, scratch=sT)))
+        db_ms = run(lambda: PT.pack_spmm(G, Bpack=Gp, out=dB, scratch=sT))
         da_ms = run(lambda: P.sddmm(G, Bp, out=dA))
         wname = workload_name(args.scale, args.deg, N, args.tiles, "f32")
         sd = frac_entry(sddmm_bytes(A.M, A.nnz, R, N, 4), da_ms, peak)
-        sd["kernel"] = "k_sddmm_lean"
-        sd["traffic"] = traffic_from_profile("k_sddmm_lean", wname)
+        sd["kernel"] = "k_sddmm_grp"
+        sd["traffic"] = traffic_from_profile("k_sddmm_grp", wname)
         out["backward"] = {
             "workload": wname, "fwd_ms": fwd_ms, "fwd_bwd_ms": fwd_ms + db_ms + da_ms,
             "dB_step_ms": db_ms, "dB_spmm": frac_entry(spmm_bytes(A.K, A.nnz, RT, N, 4), db_spmm, peak),
@@ -674,7 +707,7 @@ def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, st
         s16 = P.new_scratch(N, torch.bfloat16)
         P.pack(Bh16, out=Bp16)
         sp16 = run(lambda: P.spmm(Bp16, out=C, scratch=s16))
-        st16 = run(lambda: (P.pack(Bh16, out=Bp16), P.spmm(Bp16, out=C, scratch=s16)))
+        st16 = run(lambda: P.pack_spmm(Bh16, Bpack=Bp16, out=C, scratch=s16))
         e = frac_entry(spmm_bytes(A.M, A.nnz, R, N, 2), sp16, peak)
         out["bf16_B"] = {"spmm": e, "step_ms": st16,
                          "step_GBps_spmm_bytes": gbps(spmm_bytes(A.M, A.nnz, R, N, 2), st16),
@@ -689,7 +722,7 @@ def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, st
             sn = P.new_scratch(n, torch.float32)
             P.pack(Bn, out=Bpn)
             spmm_n = run(lambda: P.spmm(Bpn, out=Cn, scratch=sn))
-            step_n = run(lambda: (P.pack(Bn, out=Bpn), P.spmm(Bpn, out=Cn, scratch=sn)))
+            step_n = run(lambda: P.pack_spmm(Bn, Bpack=Bpn, out=Cn, scratch=sn))
             e = frac_entry(spmm_bytes(A.M, A.nnz, R, n, 4), spmm_n, peak)
             e["step_ms"] = step_n
             e["step_GBps_spmm_bytes"] = gbps(spmm_bytes(A.M, A.nnz, R, n, 4), step_n)
@@ -750,15 +783,18 @@ def form_precision(dev, stream, peak, reps, scale=22, deg=32, N=256, seed=3):
     P.pack(Bd, out=Bp)
     sp_ms = timed(lambda: P.spmm(Bp, out=C, scratch=scr), stream, reps)
     pk_ms = timed(lambda: P.pack(Bd, out=Bp), stream, reps)
-    st_ms = timed(lambda: (P.pack(Bd, out=Bp), P.spmm(Bp, out=C, scratch=scr)), stream, reps)
+    st_ms = timed(lambda: P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scr), stream, reps)
     spb = spmm_bytes(A.M, A.nnz, R, N, 2)
     wname = workload_name(scale, deg, N, 4, "bf16")
     e = frac_entry(spb, sp_ms, peak)
     e["kernel"] = spmm_kernel(N, 2)
     e["traffic"] = traffic_from_profile(spmm_kernel(N, 2), wname)
+    stp = frac_entry(spb + pack_bytes(R, N, 2), st_ms, peak)
+    stp["kernel"] = "k_spmm_lean_fused" if fused_step(N, 2) else "pack + " + spmm_kernel(N, 2)
+    stp["traffic"] = traffic_from_profile("k_spmm_lean_fused", wname) if fused_step(N, 2) else None
     return {"workload": wname, "seed": seed, "M": A.M, "nnz": A.nnz, "packed_rows": R,
             "plan_ms": plan_ms, "spmm": e, "pack": frac_entry(pack_bytes(R, N, 2), pk_ms, peak),
-            "step_ms": st_ms, "step_GBps_spmm_bytes": gbps(spb, st_ms),
+            "step": stp, "step_ms": st_ms, "step_GBps_spmm_bytes": gbps(spb, st_ms),
             "gather_bytes": A.nnz * N * 2, "gather_GBps": gbps(A.nnz * N * 2, sp_ms),
             "gflops": 2.0 * A.nnz * N / (st_ms * 1e-3) / 1e9}
 
@@ -853,13 +889,11 @@ def form_batch(dev, stream, peak, reps, G=512, N=64, seed=5):
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             for _ in range(3):
-                P.pack(Bd, out=Bp)
-                P.spmm(Bp, out=C, scratch=scratch)
+                P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scratch)
         torch.cuda.current_stream().wait_stream(side)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
-            P.pack(Bd, out=Bp)
-            P.spmm(Bp, out=C, scratch=scratch)
+            P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scratch)
         ms = timed(graph.replay, stream, reps)
         del graph
         return ms

@@ -292,6 +292,21 @@ shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const
                         int64_t ldb, int32_t N, shiro_dtype dt, void* C, int64_t ldc,
                         uint32_t flags, void* scratch, size_t scratch_bytes, void* stream);
 
+/* Pack + SpMM in one call (Sec. 5.1 stages 3 and 5 overlapped): the same results as shiro_pack
+ * (Bpack[r] = B[pack_src[r]], bit-exact) followed by shiro_spmm(plan, Bpack, ldp, B, ldb, ...)
+ * (C bit-identical: the same work items summed in the same order).  For FP32 or BF16 rows of 512
+ * bytes (N = 128 / 256) with pipeline 0 or 6, not persistent, and B, Bpack and C aligned to 16
+ * bytes, it is one launch: the plan orders the pack of row block p + 1
+ * among the SpMM work of block p (after the pack of block 0), and a warp starts an item of block p
+ * once every packed row of block p is written (a per-block count in the plan; the wait is bounded
+ * and sets a device status bit that shiro_plan_check reports if it runs out).  Otherwise it
+ * enqueues shiro_pack then shiro_spmm.  B: device K x N (ldb) of dt, read by the pack and, for
+ * local diagonal tiles, by the SpMM; Bpack: device packed_rows x N (ldp), written; C, flags,
+ * scratch: as shiro_spmm.  Calls on one plan must not overlap on the GPU. */
+shiro_status shiro_pack_spmm(shiro_plan_t plan, const void* B, int64_t ldb, int32_t N,
+                             shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,
+                             uint32_t flags, void* scratch, size_t scratch_bytes, void* stream);
+
 /* Allocation-free variant of shiro_spmm.  The paper has no counterpart: it exists for callers that
  * cannot allocate device memory for the split-row scratch -- code that runs while a stream is
  * being captured into a CUDA graph (cudaMalloc is not a capturable operation), plug-ins inside
@@ -317,18 +332,21 @@ shiro_status shiro_spmm_noalloc(shiro_plan_t plan, const void* Bpack, int64_t ld
 /* Gradient of C = A B with respect to A's stored values (a sampled dense-dense product on A's
  * pattern): dA[e] = sum_k dC[row(e), k] * Bpack[remap[e], k] (B[col[e], k] for local diagonal
  * tiles).  dC: device M x N of dt (F32/BF16 with F32 dA, or F64 with F64 dA).  The plan's
- * schedule options pick the kernel.  Unless pipeline is 5 or persistent is set, BF16 rows of 256
- * or 512 bytes and FP32 rows of 256 bytes reduce each dot product through a shared-memory tile,
- * FP32 rows of 512 bytes through a 4-wide shuffle butterfly, both within 48 registers (40 warps
- * per SM, items taken from a counter in the plan); pipeline 6 takes the tile for FP32 rows of 512
- * bytes too.  Other rows, pipeline 5 and persistent mode use an 8-wide shuffle butterfly at 64
- * registers.  Each kernel sums in a fixed order, so dA is deterministic for a given kernel. */
+ * schedule options pick the kernel.  With pipeline 0 (the default), FP32 or BF16 rows of 128, 256
+ * or 512 bytes whose rows start on 16-byte boundaries are taken by lane groups: eight lanes per
+ * nonzero, four nonzeros per warp step, a three-level shuffle sum per nonzero (48 registers, 40
+ * warps per SM, items taken from a counter in the plan).  Pipelines 3 and 6 (and pipeline 0 on
+ * rows that are not 16-byte aligned) keep the earlier 48-register kernels: BF16 rows of 256 or
+ * 512 bytes and FP32 rows of 256 bytes reduce through a shared-memory tile, FP32 rows of 512
+ * bytes through a 4-wide shuffle butterfly (pipeline 6: the tile).  Other rows, pipeline 5 and
+ * persistent mode use an 8-wide shuffle butterfly at 64 registers.  Each kernel sums in a fixed
+ * order, so dA is deterministic for a given kernel. */
 shiro_status shiro_sddmm(shiro_plan_t plan, const void* dC, int64_t lddc, const void* Bpack,
                          int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
                          void* dA, void* stream);
 
 /* Backward of C = A B: dB = A^T dC through the TRANSPOSE plan planT (pack dC by planT into
- * dCpack, then SpMM over it) and dA by shiro_sddmm on `plan`.  dB and dA may be NULL to skip
+ * dCpack, then SpMM over it, as shiro_pack_spmm) and dA by shiro_sddmm on `plan`.  dB and dA may be NULL to skip
  * them; dCpack (planT's packed_rows x N, leading dimension lddp) is needed when dB is wanted.
  * scratch must hold shiro_spmm_scratch(planT, N, dt). */
 shiro_status shiro_spmm_backward(shiro_plan_t plan, shiro_plan_t planT, const void* dC,

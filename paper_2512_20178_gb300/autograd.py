@@ -1,8 +1,9 @@
 """torch.autograd.Function for C = A B with the hand-written backward of libshiro.
 
-Forward: pack B's rows named by every tile's Cols, then SpMM over the packed rows.
-Backward: dB = A^T dC through the TRANSPOSE plan (pack dC, SpMM) and dA = SDDMM(dC, B) on A's
-pattern, reading B through the forward's packed rows.  All three run in the CUDA library.
+Forward: pack B's rows named by every tile's Cols and SpMM over the packed rows (one library
+call, shiro_pack_spmm).  Backward: dB = A^T dC through the TRANSPOSE plan (pack dC, SpMM) and
+dA = SDDMM(dC, B) on A's pattern, reading B through the forward's packed rows.  All of it runs in
+the CUDA library.
 """
 from __future__ import annotations
 
@@ -39,8 +40,9 @@ class ShiroSpMM(torch.autograd.Function):
         if val is not A.val:
             raise ValueError("val must be the value tensor the plan was built on")
         Bc = B.contiguous()
-        Bpack = A.plan.pack(Bc)
-        C = A.plan.spmm(Bpack, B=Bc)
+        Bpack = torch.empty((A.plan.info.packed_rows, Bc.shape[1]), dtype=Bc.dtype,
+                            device=Bc.device)
+        C = A.plan.pack_spmm(Bc, Bpack=Bpack)
         ctx.A = A
         ctx.save_for_backward(Bpack, Bc)
         return C

@@ -43,6 +43,7 @@ enum : int {
   ST_OFF_DIAG = 4,
   ST_OVERFLOW = 8,
   ST_COUNTER = 16,
+  ST_TIMEOUT = 32,  // a bounded device wait ran out (the kernel went on; results are not valid)
 };
 
 // One unit of SpMM/SDDMM work for one warp.
@@ -126,6 +127,13 @@ struct shiro_plan_s {
   shiro::LongRow* d_lr = nullptr;
   int32_t* d_counters = nullptr;
   int64_t items_cap = 0, slots_cap = 0, lr_cap = 0;
+  // Fused pack + SpMM: launch order (>= 0: item, < 0: pack chunk -code - 1), pack chunks
+  // {first packed row, rows, row block, 0}, per-block chunk counts and completions.
+  int32_t* d_fseq = nullptr;
+  int4* d_pchunk = nullptr;
+  int32_t* d_blk_need = nullptr;
+  int32_t* d_blk_done = nullptr;
+  int64_t fseq_cap = 0, pk_cap = 0, n_fseq = 0, n_pchunks = 0;
   // Transposed / batched copies of the planned matrix.
   int64_t* d_rowptr_own = nullptr;
   int32_t* d_col_own = nullptr;
@@ -167,5 +175,9 @@ shiro_status launch_sddmm(const shiro_plan_s* P, const void* dC, int64_t lddc, c
                           int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
                           void* dA, cudaStream_t s);
 size_t spmm_scratch_bytes(const shiro_plan_s* P, int32_t N, shiro_dtype dt);
+// Pack + SpMM (one launch for 512-byte rows, else pack then SpMM); same results as the two.
+shiro_status launch_pack_spmm(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N,
+                              shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,
+                              uint32_t flags, void* scratch, size_t scratch_bytes, cudaStream_t s);
 
 }  // namespace shiro

@@ -131,6 +131,10 @@ static void finish_shape(Shape& sh) {
   sh.cols_cap = std::max<int64_t>(1, std::min(sh.nnz, width_sum));
 }
 
+// Chunks of the fused pack + SpMM: at most 32 packed rows each, split at row-block boundaries,
+// over at most cols_cap packed rows.
+static int64_t fused_chunk_cap(const Shape& sh) { return sh.cols_cap / 32 + sh.Pr + 1; }
+
 static size_t carve(const Shape& sh, shiro_plan_s* P, char* base) {
   Carver c{base};
   const int64_t T = sh.T;
@@ -162,6 +166,12 @@ static size_t carve(const Shape& sh, shiro_plan_s* P, char* base) {
   int32_t* slot_lr = c.take<int32_t>(slots_cap);
   LongRow* lr = c.take<LongRow>(lr_cap);
   int32_t* counters = c.take<int32_t>(lr_cap);
+  // Fused pack + SpMM: chunks of at most 32 packed rows that never span two row blocks, and the
+  // launch order of chunks and items.
+  const int64_t pk_cap = fused_chunk_cap(sh);
+  int32_t* fseq = c.take<int32_t>(items_cap + pk_cap);
+  int4* pchunk = c.take<int4>(pk_cap);
+  int32_t* blk = c.take<int32_t>(2 * (int64_t)sh.Pr);
   int64_t* rowptr_own = nullptr;
   int32_t* col_own = nullptr;
   void* val_own = nullptr;
@@ -203,6 +213,12 @@ static size_t carve(const Shape& sh, shiro_plan_s* P, char* base) {
     P->d_slot_lr = slot_lr;
     P->d_lr = lr;
     P->d_counters = counters;
+    P->d_fseq = fseq;
+    P->d_pchunk = pchunk;
+    P->d_blk_need = blk;
+    P->d_blk_done = blk + sh.Pr;
+    P->fseq_cap = items_cap + pk_cap;
+    P->pk_cap = pk_cap;
     P->items_cap = items_cap;
     P->slots_cap = slots_cap;
     P->lr_cap = lr_cap;
@@ -251,6 +267,10 @@ static Temps carve_temps(const Shape& sh, char* base) {
   c.take<int32_t>(slots_cap);
   c.take<LongRow>(lr_cap);
   c.take<int32_t>(lr_cap);
+  const int64_t pk_cap = fused_chunk_cap(sh);
+  c.take<int32_t>(sh.M + slots_cap + 1 + pk_cap);
+  c.take<int4>(pk_cap);
+  c.take<int32_t>(2 * (int64_t)sh.Pr);
   if (sh.own_csr) {
     c.take<int64_t>(sh.M + 1);
     c.take<int32_t>(sh.nnz);
@@ -522,13 +542,20 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
       }
     }
   }
+  const int64_t n_chunk_items = (int64_t)items.size();
+  // Row groups never span two row blocks, so that every item belongs to one block (the fused
+  // pack + SpMM releases a block's items once the block's rows are packed).
+  const int32_t Pr = P->geo.Pr;
+  int32_t blk = 0;
   for (int64_t i = 0; i < M;) {
     const int64_t len = rp[i + 1] - rp[i];
     if (len > o.long_row_nnz) { ++i; continue; }
+    while (blk < Pr && P->rb[blk + 1] <= i) ++blk;
+    const int64_t bend = blk < Pr ? P->rb[blk + 1] : M;
     const int64_t r0 = i;
     int64_t nz = 0;
     int32_t cnt = 0;
-    while (i < M && cnt < o.group_rows) {
+    while (i < M && i < bend && cnt < o.group_rows) {
       const int64_t l = rp[i + 1] - rp[i];
       if (l > o.long_row_nnz) break;
       if (cnt > 0 && nz + l > o.group_nnz) break;
@@ -541,6 +568,56 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
   if ((int64_t)items.size() > P->items_cap || (int64_t)slot_lr.size() > P->slots_cap ||
       (int64_t)lrs.size() > P->lr_cap)
     SHIRO_FAIL(SHIRO_ERR_INSUFFICIENT_WORKSPACE, "schedule does not fit the plan workspace");
+  // Fused pack + SpMM order: the pack chunks of block 0, then for every block p its items (chunks
+  // of long rows first) with the pack chunks of block p + 1 spread over their first three
+  // quarters, so that block p + 1 is packed while block p is multiplied.
+  std::vector<int32_t> fseq;
+  std::vector<int4> pchunks;
+  std::vector<int32_t> need(Pr, 0);
+  {
+    const bool diag = P->flags & SHIRO_PLAN_DIAG_ONLY;
+    std::vector<std::vector<int32_t>> pk(Pr), sp(Pr);
+    for (int32_t p = 0; p < Pr; ++p) {
+      const int32_t t0 = diag ? p : p * P->geo.Pc, t1 = diag ? p + 1 : (p + 1) * P->geo.Pc;
+      for (int64_t r = P->pack_ptr[t0]; r < P->pack_ptr[t1]; r += 32) {
+        const int32_t cnt = (int32_t)std::min<int64_t>(32, P->pack_ptr[t1] - r);
+        pk[p].push_back(-(int32_t)pchunks.size() - 1);
+        pchunks.push_back(make_int4((int32_t)r, cnt, p, 0));
+      }
+      need[p] = (int32_t)pk[p].size();
+    }
+    // Items of each block: its chunks (in row order), then its groups (in row order).
+    int32_t b = 0;
+    for (int64_t it = 0; it < n_chunk_items; ++it) {
+      while (b < Pr && P->rb[b + 1] <= items[it].row) ++b;
+      sp[b].push_back((int32_t)it);
+    }
+    b = 0;
+    for (int64_t it = n_chunk_items; it < (int64_t)items.size(); ++it) {
+      const int64_t row = items[it].row;
+      while (b < Pr && P->rb[b + 1] <= row) ++b;
+      sp[b].push_back((int32_t)it);
+    }
+    fseq.reserve(items.size() + pchunks.size());
+    if (Pr > 0) fseq.insert(fseq.end(), pk[0].begin(), pk[0].end());
+    for (int32_t p = 0; p < Pr; ++p) {
+      const std::vector<int32_t>& S = sp[p];
+      const std::vector<int32_t> none;
+      const std::vector<int32_t>& X = p + 1 < Pr ? pk[p + 1] : none;
+      const int64_t span = std::max<int64_t>(1, (int64_t)S.size() * 3 / 4);
+      size_t xi = 0;
+      for (size_t si = 0; si < S.size(); ++si) {
+        // Chunks due by item si: ceil((si + 1) * |X| / span), all of them by the span's end.
+        const int64_t due = std::min<int64_t>((int64_t)X.size(),
+                                              ((int64_t)si + 1) * (int64_t)X.size() / span);
+        while ((int64_t)xi < due) fseq.push_back(X[xi++]);
+        fseq.push_back(S[si]);
+      }
+      while (xi < X.size()) fseq.push_back(X[xi++]);
+    }
+  }
+  if ((int64_t)fseq.size() > P->fseq_cap || (int64_t)pchunks.size() > P->pk_cap)
+    SHIRO_FAIL(SHIRO_ERR_INSUFFICIENT_WORKSPACE, "fused schedule does not fit the plan workspace");
   if (!items.empty())
     SHIRO_CUDA(cudaMemcpyAsync(P->d_items, items.data(), sizeof(Item) * items.size(),
                                cudaMemcpyHostToDevice, s));
@@ -550,8 +627,19 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
   if (!lrs.empty())
     SHIRO_CUDA(cudaMemcpyAsync(P->d_lr, lrs.data(), sizeof(LongRow) * lrs.size(),
                                cudaMemcpyHostToDevice, s));
+  if (!fseq.empty())
+    SHIRO_CUDA(cudaMemcpyAsync(P->d_fseq, fseq.data(), sizeof(int32_t) * fseq.size(),
+                               cudaMemcpyHostToDevice, s));
+  if (!pchunks.empty())
+    SHIRO_CUDA(cudaMemcpyAsync(P->d_pchunk, pchunks.data(), sizeof(int4) * pchunks.size(),
+                               cudaMemcpyHostToDevice, s));
+  if (Pr > 0)
+    SHIRO_CUDA(cudaMemcpyAsync(P->d_blk_need, need.data(), sizeof(int32_t) * Pr,
+                               cudaMemcpyHostToDevice, s));
   SHIRO_CUDA(cudaMemsetAsync(P->d_counters, 0, sizeof(int32_t) * P->lr_cap, s));
   SHIRO_CUDA(cudaStreamSynchronize(s));
+  P->n_fseq = (int64_t)fseq.size();
+  P->n_pchunks = (int64_t)pchunks.size();
   P->n_items = (int64_t)items.size();
   P->n_long = (int64_t)lrs.size();
   P->n_slots = (int64_t)slot_lr.size();

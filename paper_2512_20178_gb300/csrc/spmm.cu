@@ -18,6 +18,14 @@ SHIRO_SPMM_TYPED(spmm_f32)
 SHIRO_SPMM_TYPED(spmm_bf16)
 SHIRO_SPMM_TYPED(spmm_f64)
 #undef SHIRO_SPMM_TYPED
+#define SHIRO_FUSED_TYPED(name)                                                                  \
+  shiro_status name(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N, shiro_dtype dt, \
+                    void* Bpack, int64_t ldp, void* C, int64_t ldc, uint32_t flags,              \
+                    void* scratch, cudaStream_t s, bool* fused);
+SHIRO_FUSED_TYPED(spmm_fused_f32)
+SHIRO_FUSED_TYPED(spmm_fused_bf16)
+SHIRO_FUSED_TYPED(spmm_fused_f64)
+#undef SHIRO_FUSED_TYPED
 
 size_t spmm_scratch_bytes(const shiro_plan_s* P, int32_t N, shiro_dtype dt) {
   if (!P->n_slots) return 0;
@@ -51,6 +59,39 @@ shiro_status launch_spmm(const shiro_plan_s* P, const void* Bpack, int64_t ldp, 
   SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "value/operand dtypes: F32 with F32 or BF16, or F64 with F64");
 }
 
+shiro_status launch_pack_spmm(const shiro_plan_s* plan, const void* B, int64_t ldb, int32_t N,
+                              shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,
+                              uint32_t flags, void* scratch, size_t scratch_bytes,
+                              cudaStream_t s) {
+  // The checks of both halves first, so that nothing is launched on bad arguments.
+  if (N < 0 || ldb < N || ldp < N || ldc < N)
+    SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "bad N or leading dimension");
+  if (dt != SHIRO_F32 && dt != SHIRO_BF16 && dt != SHIRO_F64)
+    SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "unknown dtype");
+  if (N == 0 || plan->M == 0) return SHIRO_OK;
+  if (!B) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null B");
+  if (ldp > (int64_t)UINT32_MAX || ldb > (int64_t)UINT32_MAX)
+    SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "leading dimensions of B / Bpack above 2^32 - 1 elements");
+  if (!C) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null C");
+  if (!Bpack && plan->packed_rows > 0) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null Bpack");
+  if (flags & ~SHIRO_SPMM_ACCUMULATE) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "unknown SpMM flags");
+  const size_t need = spmm_scratch_bytes(plan, N, dt);
+  if (need && (!scratch || scratch_bytes < need))
+    SHIRO_FAIL(SHIRO_ERR_INSUFFICIENT_WORKSPACE, "SpMM scratch of %zu bytes, need %zu",
+               scratch_bytes, need);
+  bool fused = false;
+  if (plan->vdt == SHIRO_F32 && dt == SHIRO_F32)
+    SHIRO_TRY(spmm_fused_f32(plan, B, ldb, N, dt, Bpack, ldp, C, ldc, flags, scratch, s, &fused));
+  else if (plan->vdt == SHIRO_F32 && dt == SHIRO_BF16)
+    SHIRO_TRY(spmm_fused_bf16(plan, B, ldb, N, dt, Bpack, ldp, C, ldc, flags, scratch, s, &fused));
+  else if (plan->vdt == SHIRO_F64 && dt == SHIRO_F64)
+    SHIRO_TRY(spmm_fused_f64(plan, B, ldb, N, dt, Bpack, ldp, C, ldc, flags, scratch, s, &fused));
+  if (fused) return SHIRO_OK;
+  // Other row shapes and schedules: the two launches, same results.
+  SHIRO_TRY(launch_pack(plan, B, ldb, N, dt, Bpack, ldp, s));
+  return launch_spmm(plan, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, scratch_bytes, s);
+}
+
 }  // namespace shiro
 
 using namespace shiro;
@@ -69,6 +110,14 @@ shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const
   if (!plan) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
   return launch_spmm(plan, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, scratch_bytes,
                      (cudaStream_t)stream);
+}
+
+shiro_status shiro_pack_spmm(shiro_plan_t plan, const void* B, int64_t ldb, int32_t N,
+                            shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,
+                            uint32_t flags, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!plan) SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "null plan");
+  return launch_pack_spmm(plan, B, ldb, N, dt, Bpack, ldp, C, ldc, flags, scratch, scratch_bytes,
+                          (cudaStream_t)stream);
 }
 
 shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, const void* B,

@@ -15,8 +15,6 @@
 
 namespace shiro {
 
-constexpr int ST_TIMEOUT = 32;
-
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }

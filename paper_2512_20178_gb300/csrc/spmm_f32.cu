@@ -9,4 +9,11 @@ shiro_status spmm_f32(const shiro_plan_s* P, const void* Bpack, int64_t ldp, con
   return spmm_typed<float, float>(P, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, s);
 }
 
+shiro_status spmm_fused_f32(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N,
+                              shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,
+                              uint32_t flags, void* scratch, cudaStream_t s, bool* fused) {
+  return spmm_fused_typed<float, float>(P, B, ldb, N, dt, Bpack, ldp, C, ldc, flags, scratch, s,
+                                      fused);
+}
+
 }  // namespace shiro

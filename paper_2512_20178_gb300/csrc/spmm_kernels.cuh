@@ -714,9 +714,9 @@ static shiro_status dispatch(const shiro_plan_s* P, const SpmmParams<TV, TB>& pr
 }
 
 template <typename TV, typename TB>
-static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t ldp,
-                               const void* B, int64_t ldb, int32_t N, shiro_dtype dt, void* C,
-                               int64_t ldc, uint32_t flags, void* scratch, cudaStream_t s) {
+static SpmmParams<TV, TB> make_params(const shiro_plan_s* P, const void* Bpack, int64_t ldp,
+                                      const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
+                                      void* C, int64_t ldc, uint32_t flags, void* scratch) {
   using TA = typename AccOf<TB>::T;
   SpmmParams<TV, TB> prm{};
   prm.rowptr = P->rowptr;
@@ -746,6 +746,16 @@ static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t
                        (((uintptr_t)B % 16) == 0 && ((size_t)ldb * dtype_size(dt)) % 16 == 0));
     prm.pf_bytes = (rb % 16 == 0 && rb > 0 && rb <= (1u << 20) && al16) ? (int32_t)rb : 0;
   }
+  return prm;
+}
+
+template <typename TV, typename TB>
+static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t ldp,
+                               const void* B, int64_t ldb, int32_t N, shiro_dtype dt, void* C,
+                               int64_t ldc, uint32_t flags, void* scratch, cudaStream_t s) {
+  using TA = typename AccOf<TB>::T;
+  const SpmmParams<TV, TB> prm =
+      make_params<TV, TB>(P, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch);
   const size_t esz = dtype_size(dt);
   const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
   auto ok = [&](int vec) {
@@ -765,6 +775,74 @@ static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t
   const Variant v = pick_variant(dt, N, ok(v16), ok(v16 / 2 ? v16 / 2 : 1), ok(v16 / 4 ? v16 / 4 : 1));
   if (!v.vec) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "N=%d beyond the supported 512 columns", N);
   return dispatch<TV, TB>(P, prm, v, s);
+}
+
+template <typename TV, typename TB, int VEC, int NCH>
+static shiro_status launch_lean_fused(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                      const FusedParams<TB>& f, cudaStream_t s) {
+  constexpr int U = Occupancy<VEC, NCH, TB>::U;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm_lean_fused<TV, TB, VEC, NCH, U, true>
+                    : k_spmm_lean_fused<TV, TB, VEC, NCH, U, false>;
+  if (f.n_seq <= 0) return SHIRO_OK;
+  int per_sm = 0;
+  SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, 0));
+  const int64_t grid = std::min<int64_t>(((int64_t)f.n_seq + 1) / 2,
+                                         (int64_t)std::max(per_sm, 1) * P->sm_count);
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.work = P->d_status + 2;
+  SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));
+  SHIRO_CUDA(cudaMemsetAsync(f.done, 0, sizeof(int32_t) * (size_t)std::max(P->geo.Pr, 1), s));
+  kern<<<(unsigned)grid, 64, 0, s>>>(q, f);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
+// Pack + SpMM in one launch (k_spmm_lean_fused): FP32 / BF16 rows of 512 bytes in one fragment per
+// lane, pipeline 0 or 6, not persistent, operands aligned to the fragment.  *fused = false (nothing
+// launched) otherwise.
+template <typename TV, typename TB>
+static shiro_status spmm_fused_typed(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N,
+                                     shiro_dtype dt, void* Bpack, int64_t ldp, void* C,
+                                     int64_t ldc, uint32_t flags, void* scratch, cudaStream_t s,
+                                     bool* fused) {
+  using TA = typename AccOf<TB>::T;
+  *fused = false;
+  if constexpr (std::is_same<TB, double>::value) {
+    return SHIRO_OK;
+  } else {
+    if (P->opts.persistent || (P->opts.pipeline != 0 && P->opts.pipeline != 6)) return SHIRO_OK;
+    if (P->n_fseq > INT32_MAX) return SHIRO_OK;
+    const SpmmParams<TV, TB> prm =
+        make_params<TV, TB>(P, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch);
+    const size_t esz = dtype_size(dt);
+    // The pack reads B and writes Bpack with the gather's fragments.
+    auto ok = [&](int vec) {
+      return aligned(Bpack, ldp, esz, vec) && aligned(C, ldc, sizeof(TA), vec) &&
+             aligned(B, ldb, esz, vec);
+    };
+    const int v16 = (int)(16 / esz);
+    const Variant v =
+        pick_variant(dt, N, ok(v16), ok(v16 / 2 ? v16 / 2 : 1), ok(v16 / 4 ? v16 / 4 : 1));
+    if (v.nch != 1 || v.masked) return SHIRO_OK;
+    FusedParams<TB> f{P->d_fseq, (int32_t)P->n_fseq, P->d_pchunk, P->d_blk_need,
+                      P->d_blk_done, P->d_pack_src, (TB*)Bpack, P->geo};
+    // One launch only for rows of 512 bytes (FP32 N = 128, BF16 N = 256), where it measured
+    // faster than the two launches (R-MAT 2^20, 4x4 tiles, ms: FP32 N = 128 0.767 -> 0.750; R-MAT
+    // 2^22 BF16 N = 256 7.18 -> 7.06); narrower rows measured slower fused (FP32 N = 64 0.479 ->
+    // 0.509, BF16 N = 128 0.560 -> 0.565) and take the two launches.
+    const int row = N * (int)esz;
+    if (row != 512) return SHIRO_OK;
+    *fused = true;
+    if constexpr (std::is_same<TB, float>::value) {
+      if (v.vec == 4) return launch_lean_fused<TV, TB, 4, 1>(P, prm, f, s);
+    } else {
+      if (v.vec == 8) return launch_lean_fused<TV, TB, 8, 1>(P, prm, f, s);
+    }
+    *fused = false;
+    return SHIRO_OK;
+  }
 }
 
 }  // namespace shiro

@@ -37,7 +37,8 @@ struct LeanShape {
   static constexpr bool DYN = !(std::is_same<TB, __nv_bfloat16>::value && VEC == 4);
 };
 
-template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL, bool FULL, bool ENDS>
+template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL, bool FULL, bool ENDS,
+          bool CG = false>
 __device__ __forceinline__ void lean_batch(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
                                            const Pair<TV>* sp, int n, int off, int32_t r0, int rel,
                                            unsigned endmask,
@@ -56,7 +57,13 @@ __device__ __forceinline__ void lean_batch(const SpmmParams<TV, TB>& p, const Ba
           row = bs.b + (uint64_t)(uint32_t)(-1 - idx) * bs.ldb;
         else
           row = bs.bp + (uint64_t)(uint32_t)idx * bs.ldp;
-        gather_raw<TV, TB, VEC, NCH, false>(p, row, b[u], lane);
+        if constexpr (CG) {
+          // Rows written earlier in the same launch (fused pack + SpMM): read through L2.
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) load_raw_cg<TB, VEC>(row + c * 32 * VEC, b[u][c]);
+        } else {
+          gather_raw<TV, TB, VEC, NCH, false>(p, row, b[u], lane);
+        }
       }
     }
     // One test per step for row ends among its U nonzeros (most steps have none): a step without
@@ -90,7 +97,7 @@ __device__ __forceinline__ void lean_batch(const SpmmParams<TV, TB>& p, const Ba
 
 // Nonzeros [base, base + total) of rows r0 .. (lane l: rel = end of row r0 + l relative to base
 // if that row is non-empty, else 0).  sp holds two batches of 32 pairs.
-template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
+template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL, bool CG = false>
 __device__ __forceinline__ void lean_span(const SpmmParams<TV, TB>& p, const Bases<TB>& bs,
                                           Pair<TV>* sp, int64_t base, int total, int32_t r0,
                                           int rel, typename AccOf<TB>::T (&acc)[NCH][VEC],
@@ -122,20 +129,20 @@ __device__ __forceinline__ void lean_span(const SpmmParams<TV, TB>& p, const Bas
     const int q = rel - 1 - off;
     const unsigned endmask = __reduce_or_sync(0xffffffffu, (q >= 0 && q < 32) ? (1u << q) : 0u);
     if constexpr (LeanShape<TB, VEC>::ONE_COPY) {
-      lean_batch<TV, TB, VEC, NCH, U, LOCAL, false, true>(p, bs, cur, n, off, r0, rel, endmask,
-                                                          acc, lane);
+      lean_batch<TV, TB, VEC, NCH, U, LOCAL, false, true, CG>(p, bs, cur, n, off, r0, rel,
+                                                              endmask, acc, lane);
     } else {
       // Full batches without a row end (all chunk batches, most batches of long rows) take a copy
       // without per-nonzero tests; full batches with row ends a copy without bounds tests.
       if (n == 32 && endmask == 0)
-        lean_batch<TV, TB, VEC, NCH, U, LOCAL, true, false>(p, bs, cur, n, off, r0, rel, endmask,
-                                                            acc, lane);
+        lean_batch<TV, TB, VEC, NCH, U, LOCAL, true, false, CG>(p, bs, cur, n, off, r0, rel,
+                                                                endmask, acc, lane);
       else if (n == 32)
-        lean_batch<TV, TB, VEC, NCH, U, LOCAL, true, true>(p, bs, cur, n, off, r0, rel, endmask,
-                                                           acc, lane);
+        lean_batch<TV, TB, VEC, NCH, U, LOCAL, true, true, CG>(p, bs, cur, n, off, r0, rel,
+                                                               endmask, acc, lane);
       else
-        lean_batch<TV, TB, VEC, NCH, U, LOCAL, false, true>(p, bs, cur, n, off, r0, rel, endmask,
-                                                            acc, lane);
+        lean_batch<TV, TB, VEC, NCH, U, LOCAL, false, true, CG>(p, bs, cur, n, off, r0, rel,
+                                                                endmask, acc, lane);
     }
   }
   cp_async_wait<0>();
@@ -244,6 +251,212 @@ __global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS)
     // One span call for both kinds of item (a chunk has no row end: rel = 0 in every lane).
     lean_span<TV, TB, VEC, NCH, U, LOCAL>(p, bs, sp, item.e0, total, r0, rel, acc, lane);
     if (it < n_chunks) finish_chunk<TV, TB, VEC, NCH, false>(p, -item.tag - 1, acc, lane);
+  }
+}
+
+// ---- fused pack + SpMM (one launch) ----
+//
+// The launch walks a plan-built order of work: the pack chunks of row block 0 (Bpack[r] =
+// B[pack_src[r]], at most 32 rows each), then for every block p its SpMM items with the pack
+// chunks of block p + 1 spread among them.  A warp that takes a pack chunk copies it and counts it
+// done for its block (every lane's stores, a fence, a warp barrier, then one atomic: release); a
+// warp that takes an item of block p first waits until all of block p's chunks are counted (lane 0
+// polls with acquire loads, the warp barrier orders the other lanes after it).  The chunks of a
+// block all precede its items in the order, and a warp holding a chunk never waits, so every wait
+// ends; each is still bounded, and on expiry the warp sets ST_TIMEOUT and goes on.  Packed rows are
+// gathered through L2 (ld.global.cg): other warps of the launch wrote them.  Bpack and C are
+// bit-identical to shiro_pack followed by the SpMM (same items, same summation order).
+template <typename TB>
+struct FusedParams {
+  const int32_t* seq;     // >= 0: item index, < 0: pack chunk -code - 1
+  int32_t n_seq;
+  const int4* pchunk;     // {first packed row, rows, row block, 0}
+  const int32_t* need;    // pack chunks per row block
+  int32_t* done;          // pack chunks finished per row block (zeroed before the launch)
+  const int32_t* pack_src;
+  TB* Bpack;              // written by the pack chunks, read by the items
+  Geometry geo;
+};
+
+constexpr uint32_t kFusedSpinLimit = 1u << 22;  // x 256 ns sleeps: about a second
+#ifndef SHIRO_FUSED_PACK_U
+#define SHIRO_FUSED_PACK_U 4  // rows a lane copies at once in a pack chunk
+#endif
+#ifndef SHIRO_FUSED_PACK_STAGED
+#define SHIRO_FUSED_PACK_STAGED 1  // pack chunks staged through shared memory (cp.async)
+#endif
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename TV, typename TB, int VEC, int NCH, int U>
+__device__ __forceinline__ void fused_pack_chunk(const SpmmParams<TV, TB>& p,
+                                                 const FusedParams<TB>& f, const int4 c,
+                                                 int lane) {
+  using RF = RawFrag<TB, VEC>;
+  const TB* src0 = p.B + lane * VEC;
+  TB* dst0 = f.Bpack + lane * VEC;
+  const uint32_t ldb = (uint32_t)p.ldb, ldp = (uint32_t)p.ldp;
+  // Lane j holds the source row of the chunk's row j (one coalesced load per chunk).
+  const int32_t my_src = lane < c.y ? __ldg(f.pack_src + c.x + lane) : 0;
+#pragma unroll 1
+  for (int r = 0; r < c.y; r += U) {
+    typename RF::T w[U][NCH][RF::W];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (r + u < c.y) {  // warp-uniform
+        const int32_t s = __shfl_sync(0xffffffffu, my_src, r + u);
+        gather_raw<TV, TB, VEC, NCH, false>(p, src0 + (uint64_t)(uint32_t)s * ldb, w[u], lane);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (r + u < c.y) {
+        TB* d = dst0 + (uint64_t)(uint32_t)(c.x + r + u) * ldp;
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) store_raw<TB, VEC>(d + ch * 32 * VEC, w[u][ch]);
+      }
+    }
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicAdd(f.done + c.z, 1);
+}
+
+// The same copy staged through shared memory by cp.async: the U rows in flight cost no registers
+// (each lane reads back only its own slice, so no cross-lane wait is needed), then each lane
+// stores its slices.  stage: U rows of 32 * VEC elements for this warp.
+template <typename TV, typename TB, int VEC, int U>
+__device__ __forceinline__ void fused_pack_chunk_staged(const SpmmParams<TV, TB>& p,
+                                                        const FusedParams<TB>& f, const int4 c,
+                                                        TB* stage, int lane) {
+  constexpr int LB = VEC * (int)sizeof(TB);  // bytes of a lane's slice: 4, 8 or 16
+  constexpr int ROW = 32 * VEC;               // elements of a staged row
+  const TB* src0 = p.B + lane * VEC;
+  TB* dst0 = f.Bpack + lane * VEC;
+  const uint32_t ldb = (uint32_t)p.ldb, ldp = (uint32_t)p.ldp;
+  const uint32_t st0 = (uint32_t)__cvta_generic_to_shared(stage + lane * VEC);
+  const int32_t my_src = lane < c.y ? __ldg(f.pack_src + c.x + lane) : 0;
+#pragma unroll 1
+  for (int r = 0; r < c.y; r += U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (r + u < c.y) {  // warp-uniform
+        const int32_t s = __shfl_sync(0xffffffffu, my_src, r + u);
+        cp_async<LB>(st0 + (uint32_t)(u * ROW * (int)sizeof(TB)),
+                     src0 + (uint64_t)(uint32_t)s * ldb);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (r + u < c.y) {
+        const TB* sp = stage + u * ROW + lane * VEC;
+        if constexpr (LB == 16) {
+          const uint4 v = *reinterpret_cast<const uint4*>(sp);
+          *reinterpret_cast<uint4*>(dst0 + (uint64_t)(uint32_t)(c.x + r + u) * ldp) = v;
+        } else if constexpr (LB == 8) {
+          const uint2 v = *reinterpret_cast<const uint2*>(sp);
+          *reinterpret_cast<uint2*>(dst0 + (uint64_t)(uint32_t)(c.x + r + u) * ldp) = v;
+        } else {
+          const uint32_t v = *reinterpret_cast<const uint32_t*>(sp);
+          *reinterpret_cast<uint32_t*>(dst0 + (uint64_t)(uint32_t)(c.x + r + u) * ldp) = v;
+        }
+      }
+    }
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicAdd(f.done + c.z, 1);
+}
+
+template <typename TB>
+__device__ __forceinline__ void fused_wait_block(const FusedParams<TB>& f, int32_t blk,
+                                                 int* status, int lane) {
+  if (lane == 0) {
+    const int need = __ldg(f.need + blk);
+    uint32_t spins = 0;
+    while (ld_acquire_gpu(f.done + blk) < need) {
+      if (++spins > kFusedSpinLimit) {
+        atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+      __nanosleep(256);
+    }
+  }
+  __syncwarp();
+}
+
+template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
+__global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS)
+    k_spmm_lean_fused(const SpmmParams<TV, TB> p, const FusedParams<TB> f) {
+  using TA = typename AccOf<TB>::T;
+  __shared__ Pair<TV> s_pairs[2][64];
+  constexpr int STAGE = SHIRO_FUSED_PACK_STAGED ? SHIRO_FUSED_PACK_U * 32 * VEC : 1;
+  __shared__ __align__(16) TB s_stage[2][STAGE];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  Pair<TV>* sp = s_pairs[warp];
+  Bases<TB> bs;
+  bs.bp = f.Bpack + lane * VEC;
+  bs.b = p.B + lane * VEC;
+  bs.ldp = (uint32_t)p.ldp;
+  bs.ldb = (uint32_t)p.ldb;
+  int32_t known = -1;  // highest row block this warp has seen fully packed
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(p.work, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= f.n_seq) break;
+    const int32_t code = __ldg(f.seq + it);
+    if (code < 0) {
+      const int4 c = __ldg(f.pchunk + (-code - 1));
+      if constexpr (SHIRO_FUSED_PACK_STAGED && NCH == 1)
+        fused_pack_chunk_staged<TV, TB, VEC, SHIRO_FUSED_PACK_U>(p, f, c, s_stage[warp], lane);
+      else
+        fused_pack_chunk<TV, TB, VEC, NCH, SHIRO_FUSED_PACK_U>(p, f, c, lane);
+      continue;
+    }
+    const Item item = p.items[code];
+    // A warp takes its items in launch order, so their row blocks never decrease.
+    const int32_t blk = row_block(f.geo, item.row);
+    if (blk > known) {
+      fused_wait_block<TB>(f, blk, p.status, lane);
+      known = blk;
+    }
+    TA acc[NCH][VEC];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[c][v] = 0;
+    const bool chunk = item.tag <= 0;
+    int32_t r0 = item.row;
+    int rel = 0, total;
+    if (chunk) {
+      total = (int)min((int64_t)p.chunk, __ldg(p.rowptr + item.row + 1) - item.e0);
+    } else {
+      const int nr = item.tag;
+      const int64_t rp = lane < nr ? __ldg(p.rowptr + r0 + lane + 1) : 0;
+      rel = (int)(rp - item.e0);
+      const int prev = __shfl_up_sync(0xffffffffu, rel, 1);
+      const bool nonempty = lane < nr && rel > (lane ? prev : 0);
+      total = __shfl_sync(0xffffffffu, rel, nr - 1);
+      if (!p.accumulate) {
+        unsigned empty = __ballot_sync(0xffffffffu, lane < nr && !nonempty);
+        while (empty) {
+          const int l = __ffs(empty) - 1;
+          empty &= empty - 1;
+          flush_row<TV, TB, VEC, NCH, false>(p, r0 + l, acc, lane);
+        }
+      }
+      rel = nonempty ? rel : 0;
+    }
+    lean_span<TV, TB, VEC, NCH, U, LOCAL, true>(p, bs, sp, item.e0, total, r0, rel, acc, lane);
+    if (chunk) finish_chunk<TV, TB, VEC, NCH, false>(p, -item.tag - 1, acc, lane);
   }
 }
 

@@ -87,6 +87,63 @@ __device__ __forceinline__ void load_raw(const TB* p,
   }
 }
 
+// load_raw through L2 only (ld.global.cg): for rows that other warps of the same launch write
+// (the fused pack + SpMM), which the non-coherent path must not read.
+template <typename TB, int VEC>
+__device__ __forceinline__ void load_raw_cg(const TB* p,
+                                            typename RawFrag<TB, VEC>::T (&w)[RawFrag<TB, VEC>::W]) {
+  if constexpr (std::is_same<TB, float>::value) {
+    if constexpr (VEC == 4) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+      w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else if constexpr (VEC == 2) {
+      const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+      w[0] = v.x; w[1] = v.y;
+    } else {
+      w[0] = __ldcg(p);
+    }
+  } else if constexpr (std::is_same<TB, double>::value) {
+    if constexpr (VEC == 2) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+      w[0] = v.x; w[1] = v.y;
+    } else {
+      w[0] = __ldcg(p);
+    }
+  } else if constexpr (VEC == 8) {
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else if constexpr (VEC == 4) {
+    const uint2 v = __ldcg(reinterpret_cast<const uint2*>(p));
+    w[0] = v.x; w[1] = v.y;
+  } else if constexpr (VEC == 2) {
+    w[0] = __ldcg(reinterpret_cast<const unsigned int*>(p));
+  } else {
+    w[0] = __ldcg(reinterpret_cast<const unsigned short*>(p));
+  }
+}
+
+// Store a raw fragment as loaded (a bit-exact row copy).
+template <typename TB, int VEC>
+__device__ __forceinline__ void store_raw(TB* p,
+                                          const typename RawFrag<TB, VEC>::T (&w)[RawFrag<TB, VEC>::W]) {
+  if constexpr (std::is_same<TB, float>::value) {
+    if constexpr (VEC == 4) *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
+    else if constexpr (VEC == 2) *reinterpret_cast<float2*>(p) = make_float2(w[0], w[1]);
+    else *p = w[0];
+  } else if constexpr (std::is_same<TB, double>::value) {
+    if constexpr (VEC == 2) *reinterpret_cast<double2*>(p) = make_double2(w[0], w[1]);
+    else *p = w[0];
+  } else if constexpr (VEC == 8) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else if constexpr (VEC == 4) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+  } else if constexpr (VEC == 2) {
+    *reinterpret_cast<uint32_t*>(p) = w[0];
+  } else {
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)w[0];
+  }
+}
+
 // acc[v] = fma(a, element v of the raw fragment, acc[v]) for v = 0 .. VEC-1, in that order (the
 // BF16 widening is exact, so this equals widening first).
 template <typename TB, int VEC, typename TV>

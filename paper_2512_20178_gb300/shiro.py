@@ -80,6 +80,7 @@ SIGNATURES = [
     ("shiro_pack", ctypes.c_int, [_vp, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _vp]),
     ("shiro_spmm_scratch", ctypes.c_int, [_vp, _i32, ctypes.c_int, _P(_sz)]),
     ("shiro_spmm", ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _u32, _vp, _sz, _vp]),
+    ("shiro_pack_spmm", ctypes.c_int, [_vp, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _vp, _i64, _u32, _vp, _sz, _vp]),
     ("shiro_spmm_noalloc", ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _u32, _vp]),
     ("shiro_sddmm", ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _vp]),
     ("shiro_spmm_backward", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
@@ -368,6 +369,24 @@ class Plan:
         shiro_spmm(self.handle, _ptr(Bpack), Bpack.stride(0) if Bpack.dim() == 2 else N,
                    _ptr(B), ldb, N, dtype_code(dt), _ptr(out), out.stride(0),
                    SHIRO_SPMM_ACCUMULATE if accumulate else 0, _ptr(scratch), sb, _stream(stream))
+        return out
+
+    def pack_spmm(self, B, Bpack=None, out=None, accumulate=False, scratch=None, stream=None):
+        """Pack and SpMM in one call (shiro_pack_spmm): fills Bpack with B's packed rows and
+        returns C = A B, bit-identical to pack() then spmm()."""
+        dt = B.dtype
+        N = B.shape[1]
+        if Bpack is None:
+            Bpack = torch.empty((self.info.packed_rows, N), dtype=dt, device=B.device)
+        if out is None:
+            out = torch.empty((self.info.M, N), dtype=_ACC[dt], device=B.device)
+        if scratch is None:
+            scratch = self.new_scratch(N, dt)
+        sb = scratch.numel() if scratch is not None else 0
+        shiro_pack_spmm(self.handle, _ptr(B), B.stride(0), N, dtype_code(dt), _ptr(Bpack),
+                        Bpack.stride(0) if Bpack.dim() == 2 else N, _ptr(out), out.stride(0),
+                        SHIRO_SPMM_ACCUMULATE if accumulate else 0, _ptr(scratch), sb,
+                        _stream(stream))
         return out
 
     def sddmm(self, dC, Bpack, B=None, out=None, stream=None):

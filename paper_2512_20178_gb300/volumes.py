@@ -11,7 +11,8 @@ column (with sz_B == sz_C it is the uniform cover, mu * N * sz).  Local diagonal
 LOCAL_DIAG (1D) plan communicate nothing and report 0 everywhere.
 
 Every number comes from the library (shiro_plan_volumes and the weighted cover solver); this
-module only formats them.  Run as ``python -m paper_2512_20178_gb300.volumes --scale 20 --deg 16 --grid 4x4``
+module only formats them.  ``--census 16,64,256`` instead prints, on the host, how often a
+column repeats inside windows of consecutive rows (the evidence on tensor-core tiles).  Run as ``python -m paper_2512_20178_gb300.volumes --scale 20 --deg 16 --grid 4x4``
 (needs a GPU: the plan is built on the device).
 """
 from __future__ import annotations
@@ -36,6 +37,31 @@ def tile_volumes(plan, N: int, b_dtype: str = "f32", c_dtype: str = "f32"):
     return {"V_block": vb.numpy(), "V_col": vc.numpy(), "V_row": vr.numpy(),
             "V_joint": J["cost"].numpy(), "cover_rows": J["cover_rows"].numpy(),
             "cover_cols": J["cover_cols"].numpy()}
+
+
+def window_census(A, W: int, Pr: int = 4) -> dict:
+    """Reuse of B rows inside windows of W consecutive rows of a row block (host only).
+
+    For every window: nnz (gathers of a one-row-per-nonzero SpMM) and the number of distinct
+    columns (the B rows an MMA tile over the window, or any kernel that stages each row of the
+    window once, would read).  Reports sum(distinct) / nnz and the share of the nonzeros that sit
+    in windows whose reuse nnz / distinct reaches 1.25, 2, 4 and 8."""
+    rows = A.row_ids()
+    rb = -(-A.M // Pr)
+    p = rows // rb
+    w = p * (-(-rb // W)) + (rows - p * rb) // W
+    keys = w.astype(np.int64) * A.K + A.col.astype(np.int64)
+    uw = np.unique(keys) // A.K
+    nw = int(w.max()) + 1 if A.nnz else 1
+    nnz_w = np.bincount(w, minlength=nw)
+    dist_w = np.bincount(uw, minlength=nw)
+    reuse = np.where(nnz_w > 0, nnz_w / np.maximum(dist_w, 1), 0.0)
+    out = {"W": W, "windows_nonempty": int((nnz_w > 0).sum()),
+           "distinct_over_nnz": float(dist_w.sum() / max(1, A.nnz)),
+           "mma_density": float(A.nnz / max(1, W * dist_w.sum()))}
+    for lo in (1.25, 2, 4, 8):
+        out[f"nnz_share_reuse_ge_{lo}"] = float(nnz_w[reuse >= lo].sum() / max(1, A.nnz))
+    return out
 
 
 def format_matrix(name: str, v: np.ndarray, Pr: int, Pc: int, unit: float = 2**20) -> str:
@@ -73,11 +99,20 @@ def main(argv=None):
     ap.add_argument("--b-dtype", choices=list(SIZES), default="f32")
     ap.add_argument("--c-dtype", choices=list(SIZES), default="f32")
     ap.add_argument("--json", action="store_true")
+    ap.add_argument("--census", default="",
+                    help="comma-separated window heights: print the row-window reuse census of "
+                         "the matrix instead (host only, no GPU)")
     a = ap.parse_args(argv)
-    from . import shiro, synth
+    from . import synth
     Pr, Pc = (int(x) for x in a.grid.lower().split("x"))
     A = synth.rmat(a.scale, a.deg, a.seed) if a.graph == "rmat" else \
         synth.er(1 << a.scale, a.deg, a.seed)
+    if a.census:
+        for W in (int(x) for x in a.census.split(",")):
+            print(json.dumps({"graph": a.graph, "scale": a.scale, "deg": a.deg, "seed": a.seed,
+                              "nnz": int(A.nnz), **window_census(A, W, Pr)}))
+        return
+    from . import shiro
     d = torch.device("cuda:0")
     rp = torch.from_numpy(A.rowptr).to(d)
     col = torch.from_numpy(A.col).to(d)

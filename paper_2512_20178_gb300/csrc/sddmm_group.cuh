@@ -15,8 +15,9 @@
 // holds the sum of position j and dA is written once per batch, coalesced.
 //
 // Summation order of one dot product: each lane sums every fragment's products in element order
-// (one FMA chain per fragment), adds the fragment sums pairwise, then the eight lanes' sums are
-// added by the butterfly (xor 4, 2, 1) -- fixed, so dA is deterministic.
+// (one FMA chain per fragment: FP32 N = 128 0.722 -> 0.566 ms against one chain over all), adds
+// the fragment sums pairwise, then the eight lanes' sums are added by the butterfly (xor 4, 2, 1)
+// -- fixed, so dA is deterministic.
 #pragma once
 
 #include "internal.cuh"
@@ -27,7 +28,7 @@ namespace shiro {
 
 constexpr int SD_GRP_MIN_BLOCKS = 20;  // 2-warp CTAs per SM: 48 registers per thread
 
-// s += <g, b> over one 16-byte fragment of FP32 or BF16 storage, in element order (BF16 widened
+// s + <g, b> over one 16-byte fragment of FP32 or BF16 storage, in element order (BF16 widened
 // exactly).
 template <typename TB>
 __device__ __forceinline__ float dot_frag16(const uint4& g, const uint4& b, float s) {
@@ -37,6 +38,8 @@ __device__ __forceinline__ float dot_frag16(const uint4& g, const uint4& b, floa
     s = fmaf(__uint_as_float(g.z), __uint_as_float(b.z), s);
     s = fmaf(__uint_as_float(g.w), __uint_as_float(b.w), s);
   } else {
+    // One chain in element order (two chains, even and odd elements, measured slower for BF16
+    // N = 256: 1.03 -> 1.25 ms on R-MAT 2^20).
     const uint32_t gw[4] = {g.x, g.y, g.z, g.w};
     const uint32_t bw[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll

@@ -66,6 +66,25 @@ __device__ __forceinline__ void lean_batch(const SpmmParams<TV, TB>& p, const Ba
         }
       }
     }
+#ifndef SHIRO_LEAN_PF
+#define SHIRO_LEAN_PF 1
+#endif
+    // Rows of 512 bytes with only U = 2 in flight per warp (BF16 N = 256): bring the rows of the
+    // step two ahead into L2 while this step's gathers are in flight (the TMA unit's bulk
+    // prefetch: no registers, nothing to wait on), as the 64-register kernel does.  R-MAT 2^22,
+    // BF16 N = 256, ms: SpMM 6.19 -> 6.12, fused pack + SpMM 7.05 -> 6.80.  U = 4 at 48 registers
+    // (spills) measured 6.92.
+    constexpr bool PF = SHIRO_LEAN_PF && VEC * NCH * sizeof(TB) >= 16 && U <= 2;
+    if constexpr (PF) {
+      const int k = j + 2 * U;
+      if (p.pf_bytes && k < (FULL ? 32 : n)) {
+        const int32_t ix = sp[min(k + (lane & (U - 1)), (FULL ? 32 : n) - 1)].idx;
+        const TB* r = (LOCAL && ix < 0) ? p.B + (uint64_t)(uint32_t)(-1 - ix) * (uint64_t)p.ldb
+                                        : p.Bpack + (uint64_t)(uint32_t)ix * (uint64_t)p.ldp;
+        if (lane < U) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(r),
+                                   "r"(p.pf_bytes));
+      }
+    }
     // One test per step for row ends among its U nonzeros (most steps have none): a step without
     // one takes the FMAs alone (one copy at 48 registers: 0.617 -> 0.561 ms for FP32 N = 128).
     const unsigned em = ENDS ? (endmask >> j) & ((1u << U) - 1u) : 0u;
@@ -285,6 +304,17 @@ constexpr uint32_t kFusedSpinLimit = 1u << 22;  // x 256 ns sleeps: about a seco
 #ifndef SHIRO_FUSED_PACK_STAGED
 #define SHIRO_FUSED_PACK_STAGED 1  // pack chunks staged through shared memory (cp.async)
 #endif
+#ifndef SHIRO_FUSED_PACK_HINT
+// Evict-first L2 policy on the pack's B reads and Bpack writes, so that they displace fewer of the
+// gathered rows (ms, R-MAT 2^20 FP32 N = 128 0.758 -> 0.751; R-MAT 2^22 BF16 N = 256 6.80 -> 6.78).
+#define SHIRO_FUSED_PACK_HINT 1
+#endif
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
 
 __device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
   int v;
@@ -340,14 +370,21 @@ __device__ __forceinline__ void fused_pack_chunk_staged(const SpmmParams<TV, TB>
   const uint32_t ldb = (uint32_t)p.ldb, ldp = (uint32_t)p.ldp;
   const uint32_t st0 = (uint32_t)__cvta_generic_to_shared(stage + lane * VEC);
   const int32_t my_src = lane < c.y ? __ldg(f.pack_src + c.x + lane) : 0;
+  const uint64_t pol = SHIRO_FUSED_PACK_HINT ? l2_evict_first_policy() : 0;
 #pragma unroll 1
   for (int r = 0; r < c.y; r += U) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (r + u < c.y) {  // warp-uniform
         const int32_t s = __shfl_sync(0xffffffffu, my_src, r + u);
-        cp_async<LB>(st0 + (uint32_t)(u * ROW * (int)sizeof(TB)),
-                     src0 + (uint64_t)(uint32_t)s * ldb);
+        if constexpr (SHIRO_FUSED_PACK_HINT && LB == 16)
+          asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(
+                           st0 + (uint32_t)(u * ROW * (int)sizeof(TB))),
+                       "l"(src0 + (uint64_t)(uint32_t)s * ldb), "l"(pol)
+                       : "memory");
+        else
+          cp_async<LB>(st0 + (uint32_t)(u * ROW * (int)sizeof(TB)),
+                       src0 + (uint64_t)(uint32_t)s * ldb);
       }
     }
     cp_async_commit();
@@ -358,7 +395,13 @@ __device__ __forceinline__ void fused_pack_chunk_staged(const SpmmParams<TV, TB>
         const TB* sp = stage + u * ROW + lane * VEC;
         if constexpr (LB == 16) {
           const uint4 v = *reinterpret_cast<const uint4*>(sp);
-          *reinterpret_cast<uint4*>(dst0 + (uint64_t)(uint32_t)(c.x + r + u) * ldp) = v;
+          uint4* d = reinterpret_cast<uint4*>(dst0 + (uint64_t)(uint32_t)(c.x + r + u) * ldp);
+          if constexpr (SHIRO_FUSED_PACK_HINT)
+            asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(d),
+                         "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+                         : "memory");
+          else
+            *d = v;
         } else if constexpr (LB == 8) {
           const uint2 v = *reinterpret_cast<const uint2*>(sp);
           *reinterpret_cast<uint2*>(dst0 + (uint64_t)(uint32_t)(c.x + r + u) * ldp) = v;

@@ -264,21 +264,36 @@ def write_traffic_record(csv_path, instantiation, workload_name_, command):
     """Adds (or replaces) the record of one kernel on one workload: the mean over the captured
     launches of dram__bytes_read.sum + dram__bytes_write.sum, from an ncu raw CSV export."""
     import csv
-    rows = list(csv.reader(open(csv_path)))
+    rows = [r for r in csv.reader(open(csv_path)) if r and not r[0].startswith("==")]
     head = rows[0]
-    ci = {k: head.index(k) for k in ("Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum")}
-    units = rows[1] if len(rows) > 1 and not rows[1][ci["Kernel Name"]] else None
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
-    tot = []
     name = instantiation.split("<")[0]
-    for r in rows[1 + (units is not None):]:
-        if not r[ci["Kernel Name"]].startswith(name):
-            continue
-        b = 0.0
-        for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            u = units[ci[k]] if units else "byte"
-            b += float(r[ci[k]].replace(",", "")) * scale.get(u, 1)
-        tot.append(b)
+    want = ("dram__bytes_read.sum", "dram__bytes_write.sum")
+    tot = []
+    strip = lambda k: k.replace("void ", "").replace("shiro::", "")
+    if "Metric Name" in head:
+        # One row per (launch, metric): the --metrics --csv log.
+        ci = {k: head.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit",
+                                         "Metric Value")}
+        per = {}
+        for r in rows[1:]:
+            if not strip(r[ci["Kernel Name"]]).startswith(name) or r[ci["Metric Name"]] not in want:
+                continue
+            v = float(r[ci["Metric Value"]].replace(",", "")) * scale.get(r[ci["Metric Unit"]], 1)
+            per[r[ci["ID"]]] = per.get(r[ci["ID"]], 0.0) + v
+        tot = list(per.values())
+    else:
+        # One row per launch with a units row below the header: the --page raw --csv export.
+        ci = {k: head.index(k) for k in ("Kernel Name",) + want}
+        units = rows[1] if len(rows) > 1 and not rows[1][ci["Kernel Name"]] else None
+        for r in rows[1 + (units is not None):]:
+            if not strip(r[ci["Kernel Name"]]).startswith(name):
+                continue
+            b = 0.0
+            for k in want:
+                u = units[ci[k]] if units else "byte"
+                b += float(r[ci[k]].replace(",", "")) * scale.get(u, 1)
+            tot.append(b)
     if not tot:
         raise SystemExit(f"no launch of {name} in {csv_path}")
     try:

@@ -83,3 +83,19 @@ def test_l2_ceiling_fold_and_forms_parsing():
     assert bench.spmm_bytes(10, 20, 5, 4, 2) == 11 * 8 + 20 * 8 + 5 * 4 * 2 + 10 * 4 * 4
     assert bench.pack_bytes(5, 4, 2) == 2 * 5 * 4 * 2 + 5 * 4
     assert bench.sddmm_bytes(10, 20, 5, 4, 4) == 20 * 8 + 10 * 4 * 4 + 5 * 4 * 4 + 20 * 4
+
+
+def test_traffic_record_from_metrics_log(tmp_path, monkeypatch):
+    """The long form of ncu's --metrics --csv log (one row per launch and metric)."""
+    monkeypatch.setattr(bench, "PROFILE_TRAFFIC", str(tmp_path / "traffic.json"))
+    csv = tmp_path / "log.csv"
+    csv.write_text('==PROF== Connected to process 1\n'
+                   '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+                   '"0","void shiro::k_spmm_lean_fused<float>(P)","dram__bytes_read.sum","byte","3000"\n'
+                   '"0","void shiro::k_spmm_lean_fused<float>(P)","dram__bytes_write.sum","byte","1000"\n'
+                   '"0","void shiro::k_spmm_lean_fused<float>(P)","gpu__time_duration.sum","ns","5"\n'
+                   '"1","void shiro::k_spmm_lean_fused<float>(P)","dram__bytes_read.sum","byte","5000"\n'
+                   '"1","void shiro::k_spmm_lean_fused<float>(P)","dram__bytes_write.sum","byte","1000"\n')
+    bench.write_traffic_record(str(csv), "k_spmm_lean_fused<float>", "w", "ncu ...")
+    r = json.load(open(tmp_path / "traffic.json"))["records"][0]
+    assert r["launches"] == 2 and r["dram_bytes_per_launch"] == 5000

@@ -9,13 +9,16 @@ is built once per pattern, as in the paper, and timed on its own.
 Bytes are algorithmic, each counted once:
   SpMM  (M+1)*8 + nnz*(4 col + 4 val) + R*N*sz (packed rows) + M*N*4 (C);
   pack  2*R*N*sz + R*4 (gather read + packed write + index), R = packed rows.
-The JSON line reports:
+The step runs through the public call shiro_pack_spmm: one launch (k_spmm_lean_fused) for rows of
+512 bytes, else the pack then the SpMM.  The JSON line reports:
   value     -- SpMM bytes / step time (pack + SpMM): the SpMM's numerator over the whole step,
                the conservative reading of the headline; GB/s;
-  roofline  -- the SpMM kernel alone: SpMM bytes / its mean launch time (CUDA events on its
-               stream) vs the measured HBM copy bandwidth; with two ceilings: the HBM time of
-               those bytes, and the same kernel, schedule and gather count on a matrix whose
-               columns are folded so that every packed row stays in L2 (the gather-rate bound);
+  roofline  -- the step's kernel: for the one-launch step its pack + SpMM bytes / its mean launch
+               time (CUDA events on its stream) vs the measured HBM copy bandwidth; under
+               `spmm_kernel` the SpMM kernel alone over pre-packed rows (SpMM bytes / its launch
+               time), with two ceilings: the HBM time of those bytes, and the same kernel,
+               schedule and gather count on a matrix whose columns are folded so that every
+               packed row stays in L2 (the gather-rate bound);
   e2e       -- the same SpMM bytes over steps that also copy B from pinned host memory and C back;
   forms     -- every other configuration, each with its time, algorithmic GB/s and fraction of
                the HBM peak: the backward (dB = A^T dC, dA by SDDMM), BF16-stored B, an N sweep,

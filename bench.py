@@ -53,7 +53,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 # Every source of the library: a stored DRAM-traffic figure is used only while all are unchanged.
 KERNEL_SOURCE_GLOBS = ["paper_2512_20178_gb300/csrc/*.cu", "paper_2512_20178_gb300/csrc/*.cuh",
                        "include/shiro.h"]
-FORMS = ("backward", "bf16", "nsweep", "cusparse", "precision", "gcn", "batch", "er")
+FORMS = ("backward", "bf16", "nsweep", "autotune", "cusparse", "precision", "gcn", "batch", "er")
 
 
 def fused_step(N, sz):
@@ -747,6 +747,26 @@ def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, st
             n_sweep[str(n)] = e
             del Bn, Bpn, Cn, sn
         out["n_sweep_fp32"] = n_sweep
+    if "autotune" in fset and not bf16:
+        # The schedule the autotuner picks per N on this matrix, against the default schedule
+        # (SpMM alone over pre-packed rows, FP32).  The plan's schedule is restored afterwards.
+        tunes = {}
+        default = P.info.opts.as_dict()
+        for n in (32, 64, 128, 256):
+            Bn = torch.from_numpy(synth.dense_normal(A.K, n, 11)).to(dev)
+            Bpn = torch.empty((R, n), dtype=torch.float32, device=dev)
+            Cn = torch.empty((A.M, n), dtype=torch.float32, device=dev)
+            P.pack(Bn, out=Bpn)
+            sn = P.new_scratch(n, torch.float32)
+            d_ms = run(lambda: P.spmm(Bpn, out=Cn, scratch=sn))
+            pick = P.autotune(Bpn, C=Cn, reps=3)
+            sn = P.new_scratch(n, torch.float32)
+            t_ms = run(lambda: P.spmm(Bpn, out=Cn, scratch=sn))
+            tunes[str(n)] = {"default_ms": d_ms, "tuned_ms": t_ms, "speedup": d_ms / t_ms,
+                             "pick": pick}
+            P.reschedule(**default)
+            del Bn, Bpn, Cn, sn
+        out["autotune_fp32"] = tunes
     if "cusparse" in fset and not bf16:
         # Comparator (not on the path): cuSPARSE CSR SpMM through torch.sparse.mm, unpacked B.
         try:

@@ -135,6 +135,19 @@ __device__ __forceinline__ void sddmm_grp_item(const SddmmParams<TB>& p, int32_t
         }
         const char* br = idx >= 0 ? Bp + (uint64_t)(uint32_t)idx * ldp_b
                                   : Bl + (uint64_t)(uint32_t)(-1 - idx) * ldb_b;
+        // BF16 rows of 512 bytes: the B row of this group's position two steps ahead into L2
+        // (bulk prefetch, no registers held), issued by lane 0 of the group.  R-MAT 2^20, ms:
+        // BF16 N = 256 1.027 -> 0.927; the other shapes were slower with it (FP32 N = 128 0.566 ->
+        // 0.648, FP32 N = 64 0.421 -> 0.497, BF16 N = 128 0.502 -> 0.612), one step ahead too.
+        constexpr int PF = (std::is_same<TB, __nv_bfloat16>::value && L == 4) ? 2 : 0;
+        if constexpr (PF > 0) {
+          if (k == 0 && s + PF < 8 && j + PF < n) {
+            const int32_t ix = ci[j + PF];
+            const char* pr = ix >= 0 ? Bp - lane_off + (uint64_t)(uint32_t)ix * ldp_b
+                                     : Bl - lane_off + (uint64_t)(uint32_t)(-1 - ix) * ldb_b;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pr), "r"(L * 128));
+          }
+        }
 #pragma unroll
         for (int f = 0; f < L; ++f) b[f] = __ldg(reinterpret_cast<const uint4*>(br + f * 128));
         // One partial per fragment (independent FMA chains), added pairwise.

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(256, 4) k_spmm_grouped(const SpmmParams<TV, TB
       const LongRow L = p.lr[lr];
       int old = 0;
       if (lane == 0) {
+        __threadfence();
         old = atomicAdd(p.counters + lr, 1);
         __threadfence();
       }

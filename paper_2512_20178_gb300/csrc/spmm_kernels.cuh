@@ -288,6 +288,7 @@ __device__ __forceinline__ void finish_chunk(const SpmmParams<TV, TB>& p, int32_
   const LongRow L = p.lr[lr];
   int old = 0;
   if (lane == 0) {
+    __threadfence();  // cumulative release of the partials the barrier ordered before lane 0
     old = atomicAdd(p.counters + lr, 1);
     __threadfence();  // acquire side of the last arrival: the other chunks' partials
   }

@@ -351,9 +351,14 @@ __device__ __forceinline__ void fused_pack_chunk(const SpmmParams<TV, TB>& p,
       }
     }
   }
+  // Release: each lane's stores are fenced, the warp barrier orders them before lane 0, which
+  // fences again (cumulative over what the barrier ordered) and counts the chunk.
   __threadfence();
   __syncwarp();
-  if (lane == 0) atomicAdd(f.done + c.z, 1);
+  if (lane == 0) {
+    __threadfence();
+    atomicAdd(f.done + c.z, 1);
+  }
 }
 
 // The same copy staged through shared memory by cp.async: the U rows in flight cost no registers
@@ -412,9 +417,14 @@ __device__ __forceinline__ void fused_pack_chunk_staged(const SpmmParams<TV, TB>
       }
     }
   }
+  // Release: each lane's stores are fenced, the warp barrier orders them before lane 0, which
+  // fences again (cumulative over what the barrier ordered) and counts the chunk.
   __threadfence();
   __syncwarp();
-  if (lane == 0) atomicAdd(f.done + c.z, 1);
+  if (lane == 0) {
+    __threadfence();
+    atomicAdd(f.done + c.z, 1);
+  }
 }
 
 template <typename TB>

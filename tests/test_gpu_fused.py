@@ -137,3 +137,32 @@ def test_pack_spmm_full_size_rmat20():
                                      .astype(np.int64), np.argsort(deg)[-16:]]))
     err = gu.sampled_rows_error(A, B, C2[torch.from_numpy(rows).to(d)].cpu().numpy(), rows)
     assert err.max() <= gu.TOL
+
+
+def test_pack_spmm_in_cuda_graph():
+    """The one-launch call (its two memset nodes and the kernel) recorded in a CUDA graph and
+    replayed three times gives the eager call's bits every time."""
+    A = synth.rmat(14, 16, 160)
+    N = 128
+    B = synth.dense_normal(A.K, N, 161)
+    P = gu.plan_of(A, 4, 4)
+    d = gu.dev()
+    Bd = torch.from_numpy(B).to(d)
+    Bp = torch.empty((P.info.packed_rows, N), device=d)
+    C = torch.empty((A.M, N), device=d)
+    scr = P.new_scratch(N, torch.float32)
+    ref = P.pack_spmm(Bd, Bpack=torch.empty_like(Bp), scratch=scr).clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scr)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        P.pack_spmm(Bd, Bpack=Bp, out=C, scratch=scr)
+    for _ in range(3):
+        C.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        P.check()
+        assert torch.equal(C, ref)

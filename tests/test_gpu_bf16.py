@@ -65,8 +65,15 @@ def test_full_size_precision_rmat22_deg32_n256():
     P = gu.plan_of(A, 4, 4)
     d = gu.dev()
     Bd = torch.from_numpy(bits.view(np.int16)).to(d).view(torch.bfloat16)
-    C = P.spmm(P.pack(Bd))
+    Bp = P.pack(Bd)
+    C = P.spmm(Bp)
+    # The one-launch pack + SpMM the bench times: the same bits.
+    Bp2 = torch.empty_like(Bp)
+    C2 = P.pack_spmm(Bd, Bpack=Bp2)
     torch.cuda.synchronize()
+    P.check()
+    assert torch.equal(Bp2.view(torch.int16), Bp.view(torch.int16)) and torch.equal(C2, C)
+    del Bp, Bp2, C2
     deg = np.diff(A.rowptr)
     rows = np.unique(np.concatenate([
         (synth.uniform_f64(7, synth.STREAM_PERM, 0, 1500) * A.M).astype(np.int64),

@@ -173,7 +173,8 @@ def test_full_size_rmat20_sampled_rows(rmat20):
 
 
 @pytest.mark.parametrize("case", ["f32_n128", "f32_n256", "f32_n64", "f32_n32", "bf16_n128",
-                                  "bf16_n256", "f64_n128", "local_diag", "accumulate", "hub"])
+                                  "bf16_n256", "bf16_n64", "f64_n128", "local_diag", "accumulate",
+                                  "hub", "narrow_local_diag", "narrow_accumulate", "narrow_hub"])
 def test_pipelines_bit_identical(case):
     """Register gathers (64- and 48-register forms), per-lane async copies and TMA bulk copies in
     two stages, and the per-lane copy ring sum every row in the same order, so all pipelines give
@@ -189,14 +190,16 @@ def test_pipelines_bit_identical(case):
         N = 32
     elif case.startswith("bf16"):
         dt = torch.bfloat16
-        N = 256 if case.endswith("256") else 128
+        N = int(case.split("_n")[1])
     elif case == "f64_n128":
         vdt, dt = torch.float64, torch.float64
-    elif case == "local_diag":
+    if case.startswith("narrow"):
+        N = 32  # rows of 128 bytes
+    if case.endswith("local_diag"):
         flags = shiro.SHIRO_PLAN_LOCAL_DIAG
-    elif case == "accumulate":
+    elif case.endswith("accumulate"):
         acc = True
-    elif case == "hub":
+    elif case.endswith("hub"):
         A = synth.hub_matrix(64, 1 << 16, 5, 1 << 16, 2, 132)
     B = synth.dense_normal(A.K, N, 133)
     if dt == torch.bfloat16:

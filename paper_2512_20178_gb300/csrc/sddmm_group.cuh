@@ -10,7 +10,8 @@
 //
 // Per batch of 32 nonzeros (indices staged in shared memory by cp.async one batch ahead), group g
 // takes positions 8g .. 8g + 7 in order, so consecutive nonzeros of a row stay in one group and
-// its dC fragments are reloaded only when the row changes.  The row of every position comes from
+// its dC fragments are reloaded only when the row changes; BF16 rows of 512 bytes keep the B
+// row of the group's next position in flight as well (SdgShape).  The row of every position comes from
 // a warp max-scan over the starts of the item's non-empty rows.  After the eight steps lane j
 // holds the sum of position j and dA is written once per batch, coalesced.
 //
@@ -26,7 +27,18 @@
 
 namespace shiro {
 
-constexpr int SD_GRP_MIN_BLOCKS = 20;  // 2-warp CTAs per SM: 48 registers per thread
+// Per row shape, the gathers in flight per group and the register budget (2-warp CTAs per SM):
+// BF16 rows of 512 bytes keep two B rows in flight per group (the row of step s + 1 is loaded
+// before step s's dot) at 64 registers, 16 CTAs per SM; the other shapes one row per group at 48
+// registers, 20 CTAs per SM, with the eight steps unrolled.  R-MAT 2^20, 4x4 tiles, ms (one row
+// with the steps in a loop -> unrolled -> two rows, 64 registers): FP32 N = 128 0.572 -> 0.554 ->
+// 0.621, FP32 N = 64 0.428 -> 0.410 -> 0.449, BF16 N = 256 0.931 -> 0.910 -> 0.807, BF16 N = 128
+// 0.507 -> 0.493 -> 0.523; two rows at 48 registers spilled (FP32 N = 128 0.988).
+template <typename TB, int L>
+struct SdgShape {
+  static constexpr int DEPTH = (std::is_same<TB, __nv_bfloat16>::value && L == 4) ? 2 : 1;
+  static constexpr int MIN_BLOCKS = DEPTH == 2 ? 16 : 20;
+};
 
 // s + <g, b> over one 16-byte fragment of FP32 or BF16 storage, in element order (BF16 widened
 // exactly).
@@ -51,9 +63,29 @@ __device__ __forceinline__ float dot_frag16(const uint4& g, const uint4& b, floa
   return s;
 }
 
+// L 16-byte fragments at stride 128 bytes from p (this lane's slices of a row).
+template <int L>
+__device__ __forceinline__ void load_frags(const char* p, uint4 (&v)[L]) {
+#pragma unroll
+  for (int f = 0; f < L; ++f) v[f] = __ldg(reinterpret_cast<const uint4*>(p + f * 128));
+}
+
+// One partial per fragment (independent FMA chains, element order within each), added pairwise.
+template <typename TB, int L>
+__device__ __forceinline__ float grp_dot(const uint4 (&g)[L], const uint4 (&b)[L]) {
+  float part[L];
+#pragma unroll
+  for (int f = 0; f < L; ++f) part[f] = dot_frag16<TB>(g[f], b[f], 0.f);
+#pragma unroll
+  for (int w = 1; w < L; w <<= 1)
+#pragma unroll
+    for (int f = 0; f + w < L; f += 2 * w) part[f] += part[f + w];
+  return part[0];
+}
+
 // One work item (a group of rows or a chunk of a long row).  sidx: 2 x 32 staged indices;
 // srow: 32 item-local rows of the batch's positions.
-template <typename TB, int L>
+template <typename TB, int L, int DEPTH>
 __device__ __forceinline__ void sddmm_grp_item(const SddmmParams<TB>& p, int32_t* sidx,
                                                int32_t* srow, const Item& item, int lane) {
   const bool chunk = item.tag <= 0;
@@ -118,52 +150,57 @@ __device__ __forceinline__ void sddmm_grp_item(const SddmmParams<TB>& p, int32_t
     const int32_t* ci = sidx + h * 32;
     const int n = min(32, total - off);
     float out = 0.f;
-#pragma unroll 1
-    for (int s = 0; s < 8; ++s) {
-      const int j = grp * 8 + s;
-      const bool valid = j < n;
-      float acc = 0.f;
-      if (valid) {
-        const int row = srow[j];
-        const int32_t idx = ci[j];
-        uint4 b[L];
-        if (row != cur) {
-          const char* dr = dC + (uint64_t)(uint32_t)(r0 + row) * lddc_b;
+    // This lane's slice of the B row of batch position j (a packed row, or a row of B itself for
+    // a LOCAL_DIAG tile) and the dC row of position j, loaded when the row changes.
+    auto brow = [&](int j) {
+      const int32_t idx = ci[j];
+      return idx >= 0 ? Bp + (uint64_t)(uint32_t)idx * ldp_b
+                      : Bl + (uint64_t)(uint32_t)(-1 - idx) * ldb_b;
+    };
+    auto dc_row = [&](int j) {
+      const int row = srow[j];
+      if (row != cur) {
+        const char* dr = dC + (uint64_t)(uint32_t)(r0 + row) * lddc_b;
 #pragma unroll
-          for (int f = 0; f < L; ++f) g[f] = __ldg(reinterpret_cast<const uint4*>(dr + f * 128));
-          cur = row;
-        }
-        const char* br = idx >= 0 ? Bp + (uint64_t)(uint32_t)idx * ldp_b
-                                  : Bl + (uint64_t)(uint32_t)(-1 - idx) * ldb_b;
-        // BF16 rows of 512 bytes: the B row of this group's position two steps ahead into L2
-        // (bulk prefetch, no registers held), issued by lane 0 of the group.  R-MAT 2^20, ms:
-        // BF16 N = 256 1.027 -> 0.927; the other shapes were slower with it (FP32 N = 128 0.566 ->
-        // 0.648, FP32 N = 64 0.421 -> 0.497, BF16 N = 128 0.502 -> 0.612), one step ahead too.
-        constexpr int PF = (std::is_same<TB, __nv_bfloat16>::value && L == 4) ? 2 : 0;
-        if constexpr (PF > 0) {
-          if (k == 0 && s + PF < 8 && j + PF < n) {
-            const int32_t ix = ci[j + PF];
-            const char* pr = ix >= 0 ? Bp - lane_off + (uint64_t)(uint32_t)ix * ldp_b
-                                     : Bl - lane_off + (uint64_t)(uint32_t)(-1 - ix) * ldb_b;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pr), "r"(L * 128));
-          }
-        }
-#pragma unroll
-        for (int f = 0; f < L; ++f) b[f] = __ldg(reinterpret_cast<const uint4*>(br + f * 128));
-        // One partial per fragment (independent FMA chains), added pairwise.
-        float part[L];
-#pragma unroll
-        for (int f = 0; f < L; ++f) part[f] = dot_frag16<TB>(g[f], b[f], 0.f);
-#pragma unroll
-        for (int w = 1; w < L; w <<= 1)
-#pragma unroll
-          for (int f = 0; f + w < L; f += 2 * w) part[f] += part[f + w];
-        acc = part[0];
+        for (int f = 0; f < L; ++f) g[f] = __ldg(reinterpret_cast<const uint4*>(dr + f * 128));
+        cur = row;
       }
+    };
+    // After step s, lane k == s of each group keeps its group's dot product.
+    auto finish = [&](float acc, int s) {
       acc += __shfl_xor_sync(FULLM, acc, 4);
       acc += __shfl_xor_sync(FULLM, acc, 2);
       acc += __shfl_xor_sync(FULLM, acc, 1);
       if (k == s) out = acc;
+    };
+    if constexpr (DEPTH == 2) {
+      // Two gathers in flight per group: the B row of step s + 1 is loaded before step s's dot.
+      uint4 bq[2][L];
+      if (grp * 8 < n) load_frags<L>(brow(grp * 8), bq[0]);
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int j = grp * 8 + s;
+        if (s + 1 < 8 && j + 1 < n) load_frags<L>(brow(j + 1), bq[(s + 1) & 1]);
+        float acc = 0.f;
+        if (j < n) {
+          dc_row(j);
+          acc = grp_dot<TB, L>(g, bq[s & 1]);
+        }
+        finish(acc, s);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int j = grp * 8 + s;
+        float acc = 0.f;
+        if (j < n) {
+          dc_row(j);
+          uint4 b[L];
+          load_frags<L>(brow(j), b);
+          acc = grp_dot<TB, L>(g, b);
+        }
+        finish(acc, s);
+      }
     }
     if (lane < n) p.dA[item.e0 + off + lane] = out;
   }
@@ -172,7 +209,8 @@ __device__ __forceinline__ void sddmm_grp_item(const SddmmParams<TB>& p, int32_t
 
 // SMs x resident blocks of two warps; every warp takes the next item from the plan's counter.
 template <typename TB, int L>
-__global__ void __launch_bounds__(64, SD_GRP_MIN_BLOCKS) k_sddmm_grp(const SddmmParams<TB> p) {
+__global__ void __launch_bounds__(64, (SdgShape<TB, L>::MIN_BLOCKS))
+    k_sddmm_grp(const SddmmParams<TB> p) {
   __shared__ __align__(16) int32_t s_idx[2][64];
   __shared__ __align__(16) int32_t s_row[2][32];
   const int lane = threadIdx.x & 31;
@@ -182,7 +220,8 @@ __global__ void __launch_bounds__(64, SD_GRP_MIN_BLOCKS) k_sddmm_grp(const Sddmm
     if (lane == 0) it = atomicAdd(p.work, 1);
     it = __shfl_sync(FULLM, it, 0);
     if ((int64_t)it >= p.n_items) break;
-    sddmm_grp_item<TB, L>(p, s_idx[warp], s_row[warp], p.items[it], lane);
+    sddmm_grp_item<TB, L, SdgShape<TB, L>::DEPTH>(p, s_idx[warp], s_row[warp], p.items[it],
+                                                   lane);
   }
 }
 

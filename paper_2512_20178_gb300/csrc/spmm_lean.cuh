@@ -22,6 +22,24 @@ namespace shiro {
 // Measured against 24 (40 registers) on R-MAT 2^20, 4x4 tiles: 48 registers is as fast or faster
 // for FP32 N = 128 and clearly faster for FP32 N = 64 and BF16 N = 128 / 256.
 constexpr int LEAN_MIN_BLOCKS = 20;
+// Steps of the batch loop unrolled, per row shape (one step = U gathers, then their FMAs):
+// unrolling lets the next step's gathers issue before this step's FMAs, which pays where a step
+// is short (narrow rows) and spills where it is long.  R-MAT 2^20, 4x4 tiles, SpMM ms by unroll
+// factor 1 / 2 / 4 / 8: FP32 N = 32 0.336 / 0.293 / 0.294 / 0.308; FP32 N = 64 0.370 / 0.381 /
+// 0.364; BF16 N = 64 0.359 / 0.356 / 0.316 / 0.366; BF16 N = 128 0.444 / 0.447 / 0.461; FP32 N =
+// 128 0.552 / 0.785 (spills).
+#ifndef SHIRO_LU_F32V1
+#define SHIRO_LU_F32V1 2
+#endif
+#ifndef SHIRO_LU_F32V2
+#define SHIRO_LU_F32V2 4
+#endif
+#ifndef SHIRO_LU_BF16V2
+#define SHIRO_LU_BF16V2 4
+#endif
+#ifndef SHIRO_LU_BF16V4
+#define SHIRO_LU_BF16V4 1
+#endif
 
 // FP32 rows in float4 fragments (16 registers per U = 4 rows in flight) take one loop copy for
 // full and partial batches: three copies spill there (112 bytes at 48 registers), and so does a
@@ -35,6 +53,9 @@ struct LeanShape {
   // warp -> counter): FP32 N = 128 0.567 -> 0.554, N = 64 0.391 -> 0.371, N = 32 0.355 -> 0.331,
   // BF16 N = 256 0.815 -> 0.769 (R-MAT 2^22: 6.52 -> 6.16), BF16 N = 128 0.453 -> 0.474.
   static constexpr bool DYN = !(std::is_same<TB, __nv_bfloat16>::value && VEC == 4);
+  static constexpr bool F32 = std::is_same<TB, float>::value;
+  static constexpr int UNROLL = F32 ? (VEC == 1 ? SHIRO_LU_F32V1 : VEC == 2 ? SHIRO_LU_F32V2 : 1)
+                                    : (VEC == 2 ? SHIRO_LU_BF16V2 : VEC == 4 ? SHIRO_LU_BF16V4 : 1);
 };
 
 template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL, bool FULL, bool ENDS,
@@ -44,7 +65,7 @@ __device__ __forceinline__ void lean_batch(const SpmmParams<TV, TB>& p, const Ba
                                            unsigned endmask,
                                            typename AccOf<TB>::T (&acc)[NCH][VEC], int lane) {
   static_assert(32 % U == 0, "U must divide the 32-pair batch");
-#pragma unroll 1
+#pragma unroll LeanShape<TB, VEC>::UNROLL
   for (int j = 0; j < (FULL ? 32 : n); j += U) {
     typename RawFrag<TB, VEC>::T b[U][NCH][RawFrag<TB, VEC>::W];
 #pragma unroll

@@ -616,7 +616,7 @@ static shiro_status launch_lring(const shiro_plan_s* P, const SpmmParams<TV, TB>
 template <typename TV, typename TB, int VEC, int NCH>
 static shiro_status launch_lean(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
                                 cudaStream_t s) {
-  constexpr int U = Occupancy<VEC, NCH, TB>::U;
+  constexpr int U = LeanShape<TB, VEC>::WIDE ? SHIRO_LEAN_UW : Occupancy<VEC, NCH, TB>::U;
   const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
   auto kern = local ? k_spmm_lean<TV, TB, VEC, NCH, U, true>
                     : k_spmm_lean<TV, TB, VEC, NCH, U, false>;
@@ -781,7 +781,7 @@ static shiro_status spmm_typed(const shiro_plan_s* P, const void* Bpack, int64_t
 template <typename TV, typename TB, int VEC, int NCH>
 static shiro_status launch_lean_fused(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
                                       const FusedParams<TB>& f, cudaStream_t s) {
-  constexpr int U = Occupancy<VEC, NCH, TB>::U;
+  constexpr int U = LeanShape<TB, VEC>::WIDE ? SHIRO_LEAN_UW : Occupancy<VEC, NCH, TB>::U;
   const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
   auto kern = local ? k_spmm_lean_fused<TV, TB, VEC, NCH, U, true>
                     : k_spmm_lean_fused<TV, TB, VEC, NCH, U, false>;

@@ -22,6 +22,17 @@ namespace shiro {
 // Measured against 24 (40 registers) on R-MAT 2^20, 4x4 tiles: 48 registers is as fast or faster
 // for FP32 N = 128 and clearly faster for FP32 N = 64 and BF16 N = 128 / 256.
 constexpr int LEAN_MIN_BLOCKS = 20;
+// BF16 rows of 512 bytes: rows in flight per warp and CTAs per SM.  Measured (ms; R-MAT 2^20 SpMM,
+// R-MAT 2^22 avg degree 32 SpMM / pack + SpMM): U = 2, 20 CTAs (48 registers) 0.824, 6.01 / 6.72;
+// U = 4, 16 CTAs (64 registers, 40-60 bytes spilled) 0.776, 6.34 / 6.64; U = 2, 16 CTAs 0.826,
+// 6.25 / 7.06; U = 4, 12 CTAs 0.789, 6.38 / 7.46.  More rows per warp pay where the gathers hit
+// L2 and lose where they go to HBM (the full-size workload), so the default stays.
+#ifndef SHIRO_LEAN_MINB_W
+#define SHIRO_LEAN_MINB_W 20
+#endif
+#ifndef SHIRO_LEAN_UW
+#define SHIRO_LEAN_UW 2
+#endif
 // Steps of the batch loop unrolled, per row shape (one step = U gathers, then their FMAs):
 // unrolling lets the next step's gathers issue before this step's FMAs, which pays where a step
 // is short (narrow rows) and spills where it is long.  R-MAT 2^20, 4x4 tiles, SpMM ms by unroll
@@ -54,6 +65,9 @@ struct LeanShape {
   // BF16 N = 256 0.815 -> 0.769 (R-MAT 2^22: 6.52 -> 6.16), BF16 N = 128 0.453 -> 0.474.
   static constexpr bool DYN = !(std::is_same<TB, __nv_bfloat16>::value && VEC == 4);
   static constexpr bool F32 = std::is_same<TB, float>::value;
+  // BF16 rows of 512 bytes (eight FP32 accumulators per lane).
+  static constexpr bool WIDE = std::is_same<TB, __nv_bfloat16>::value && VEC == 8;
+  static constexpr int MIN_BLOCKS = WIDE ? SHIRO_LEAN_MINB_W : LEAN_MIN_BLOCKS;
   static constexpr int UNROLL = F32 ? (VEC == 1 ? SHIRO_LU_F32V1 : VEC == 2 ? SHIRO_LU_F32V2 : 1)
                                     : (VEC == 2 ? SHIRO_LU_BF16V2 : VEC == 4 ? SHIRO_LU_BF16V4 : 1);
 };
@@ -191,7 +205,8 @@ __device__ __forceinline__ void lean_span(const SpmmParams<TV, TB>& p, const Bas
 // Blocks [0, chunk_blocks) run the chunks of long rows, the others the row groups; two warps per
 // block, one item per warp (no persistent mode).
 template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
-__global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS) k_spmm_lean(const SpmmParams<TV, TB> p) {
+__global__ void __launch_bounds__(64, (LeanShape<TB, VEC>::MIN_BLOCKS))
+    k_spmm_lean(const SpmmParams<TV, TB> p) {
   using TA = typename AccOf<TB>::T;
   __shared__ Pair<TV> s_pairs[2][64];
   const int lane = threadIdx.x & 31;
@@ -243,7 +258,7 @@ __global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS) k_spmm_lean(const SpmmPar
 // whose item ends early does not wait for its block's other warp.  Kept apart from k_spmm_lean:
 // a loop around both item paths costs that kernel registers.
 template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
-__global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS)
+__global__ void __launch_bounds__(64, (LeanShape<TB, VEC>::MIN_BLOCKS))
     k_spmm_lean_dyn(const SpmmParams<TV, TB> p) {
   using TA = typename AccOf<TB>::T;
   __shared__ Pair<TV> s_pairs[2][64];
@@ -466,7 +481,7 @@ __device__ __forceinline__ void fused_wait_block(const FusedParams<TB>& f, int32
 }
 
 template <typename TV, typename TB, int VEC, int NCH, int U, bool LOCAL>
-__global__ void __launch_bounds__(64, LEAN_MIN_BLOCKS)
+__global__ void __launch_bounds__(64, (LeanShape<TB, VEC>::MIN_BLOCKS))
     k_spmm_lean_fused(const SpmmParams<TV, TB> p, const FusedParams<TB> f) {
   using TA = typename AccOf<TB>::T;
   __shared__ Pair<TV> s_pairs[2][64];

@@ -175,6 +175,14 @@ shiro_status launch_sddmm(const shiro_plan_s* P, const void* dC, int64_t lddc, c
                           int64_t ldp, const void* B, int64_t ldb, int32_t N, shiro_dtype dt,
                           void* dA, cudaStream_t s);
 size_t spmm_scratch_bytes(const shiro_plan_s* P, int32_t N, shiro_dtype dt);
+// cudaOccupancyMaxActiveBlocksPerMultiprocessor, asked once per (device, kernel, block size,
+// dynamic shared memory) and then answered from a table (the grid-sizing query otherwise costs
+// host time on every launch).
+cudaError_t occupancy_cached(int* per_sm, const void* kern, int threads, size_t smem);
+template <typename K>
+inline cudaError_t blocks_per_sm(int* per_sm, K kern, int threads, size_t smem) {
+  return occupancy_cached(per_sm, reinterpret_cast<const void*>(kern), threads, smem);
+}
 // Pack + SpMM (one launch for 512-byte rows, else pack then SpMM); same results as the two.
 shiro_status launch_pack_spmm(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N,
                               shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,

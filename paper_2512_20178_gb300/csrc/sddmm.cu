@@ -239,8 +239,7 @@ static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& p
       if (!prm.persistent && P->opts.pipeline == 0 && ok16) {
         if (prm.n_items > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
         int per_sm = 0;
-        SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_sddmm_grp<TB, RB / 128>, 64, 0));
+        SHIRO_CUDA(blocks_per_sm(&per_sm, k_sddmm_grp<TB, RB / 128>, 64, 0));
         const int64_t grid = std::min<int64_t>((prm.n_items + 1) / 2,
                                                (int64_t)std::max(per_sm, 1) * P->sm_count);
         if (grid <= 0) return SHIRO_OK;
@@ -278,11 +277,9 @@ static shiro_status sddmm_launch(const shiro_plan_s* P, const SddmmParams<TB>& p
       SddmmParams<TB> q = prm;
       int per_sm = 0;
       if (tile)
-        SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_sddmm_lean<TB, VEC, true>, 64, 0));
+        SHIRO_CUDA(blocks_per_sm(&per_sm, k_sddmm_lean<TB, VEC, true>, 64, 0));
       else
-        SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_sddmm_lean<TB, VEC, (BF || VEC != 4)>, 64, 0));
+        SHIRO_CUDA(blocks_per_sm(&per_sm, k_sddmm_lean<TB, VEC, (BF || VEC != 4)>, 64, 0));
       grid = std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * P->sm_count);
       q.work = P->d_status + 2;
       SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));

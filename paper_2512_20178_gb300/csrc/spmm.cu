@@ -4,10 +4,45 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
 namespace shiro {
+
+namespace {
+struct OccKey {
+  int device;
+  const void* kern;
+  int threads;
+  size_t smem;
+  bool operator==(const OccKey& o) const {
+    return device == o.device && kern == o.kern && threads == o.threads && smem == o.smem;
+  }
+};
+std::mutex g_occ_mu;
+std::vector<std::pair<OccKey, int>> g_occ;  // a few dozen kernel shapes at most
+}  // namespace
+
+cudaError_t occupancy_cached(int* per_sm, const void* kern, int threads, size_t smem) {
+  OccKey k{0, kern, threads, smem};
+  cudaError_t e = cudaGetDevice(&k.device);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    for (const auto& kv : g_occ)
+      if (kv.first == k) {
+        *per_sm = kv.second;
+        return cudaSuccess;
+      }
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ.emplace_back(k, *per_sm);
+  return cudaSuccess;
+}
 
 // One translation unit per storage type (spmm_f32.cu, spmm_bf16.cu, spmm_f64.cu).
 #define SHIRO_SPMM_TYPED(name)                                                                  \

@@ -461,7 +461,7 @@ static shiro_status launch_async_batch(const shiro_plan_s* P, const SpmmParams<T
   int64_t gblocks = (n_groups + wpc - 1) / wpc;
   if (prm.persistent) {
     int per_sm = 0;
-    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, smem));
+    SHIRO_CUDA(blocks_per_sm(&per_sm, kern, wpc * 32, smem));
     gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
   }
   const int64_t grid = q.chunk_blocks + gblocks;
@@ -501,7 +501,7 @@ static shiro_status launch_bulk_batch(const shiro_plan_s* P, const SpmmParams<TV
   int64_t gblocks = (n_groups + wpc - 1) / wpc;
   if (prm.persistent) {
     int per_sm = 0;
-    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, smem));
+    SHIRO_CUDA(blocks_per_sm(&per_sm, kern, wpc * 32, smem));
     gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
   }
   const int64_t grid = q.chunk_blocks + gblocks;
@@ -527,7 +527,7 @@ static shiro_status launch_grouped(const shiro_plan_s* P, const SpmmParams<TV, T
   int64_t gblocks = (n_groups + wpc - 1) / wpc;
   if (prm.persistent) {
     int per_sm = 0;
-    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, 0));
+    SHIRO_CUDA(blocks_per_sm(&per_sm, kern, wpc * 32, 0));
     gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
   }
   const int64_t grid = q.chunk_blocks + gblocks;
@@ -582,7 +582,7 @@ static shiro_status launch_lring_rg(const shiro_plan_s* P, const SpmmParams<TV, 
   int64_t gblocks = (n_groups + wpc - 1) / wpc;
   if (prm.persistent) {
     int per_sm = 0;
-    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpc * 32, smem));
+    SHIRO_CUDA(blocks_per_sm(&per_sm, kern, wpc * 32, smem));
     gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
   }
   const int64_t grid = q.chunk_blocks + gblocks;
@@ -634,7 +634,7 @@ static shiro_status launch_lean(const shiro_plan_s* P, const SpmmParams<TV, TB>&
     // Persistent: SMs x resident CTAs, every warp takes the next item from a counter.
     if (prm.n_items > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
     int per_sm = 0;
-    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, 0));
+    SHIRO_CUDA(blocks_per_sm(&per_sm, kern, 64, 0));
     grid = std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * P->sm_count);
     q.work = P->d_status + 2;
     SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));
@@ -683,7 +683,7 @@ static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& 
   int64_t gblocks = (n_groups + wpc - 1) / wpc;
   if (prm.persistent) {
     int per_sm = 0;
-    SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    SHIRO_CUDA(blocks_per_sm(&per_sm, kern, threads, 0));
     gblocks = std::min<int64_t>(gblocks, (int64_t)std::max(per_sm, 1) * P->sm_count);
   }
   const int64_t grid = q.chunk_blocks + gblocks;
@@ -787,7 +787,7 @@ static shiro_status launch_lean_fused(const shiro_plan_s* P, const SpmmParams<TV
                     : k_spmm_lean_fused<TV, TB, VEC, NCH, U, false>;
   if (f.n_seq <= 0) return SHIRO_OK;
   int per_sm = 0;
-  SHIRO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, 0));
+  SHIRO_CUDA(blocks_per_sm(&per_sm, kern, 64, 0));
   const int64_t grid = std::min<int64_t>(((int64_t)f.n_seq + 1) / 2,
                                          (int64_t)std::max(per_sm, 1) * P->sm_count);
   SpmmParams<TV, TB> q = prm;

@@ -87,7 +87,10 @@ typedef struct {
 /* Work schedule of the SpMM/SDDMM kernels (zero fields take the defaults).  Rows with more than
  * long_row_nnz nonzeros are split into chunks of chunk_nnz (>= 32) nonzeros whose FP32 partial
  * sums are added in a fixed order (deterministic); shorter rows are grouped into work items of at
- * most group_nnz nonzeros and group_rows rows.  One warp runs one work item at a time. */
+ * most group_nnz nonzeros and group_rows rows.  One warp runs one work item at a time.
+ * group_nnz 0 (the default) is automatic: 256, or fewer when the matrix is small enough that
+ * 256-nonzero groups would leave warp slots without an item (at most the short rows' nonzeros
+ * over SMs x 40).  Rows are never split by a group, so results do not depend on group_nnz. */
 typedef struct {
   int32_t long_row_nnz;
   int32_t chunk_nnz;
@@ -385,8 +388,8 @@ shiro_status shiro_autotune(shiro_plan_t plan, const void* Bpack, int64_t ldp, c
  * compute calls use the thread's current device; streams passed in must belong to it. */
 shiro_status shiro_set_device(int32_t device);
 
-/* Default schedule options: long_row_nnz 512, chunk_nnz 256, group_nnz 256, group_rows 32,
- * warps_per_cta 1, persistent 0, pipeline 0, stage_rows 0. */
+/* Default schedule options: long_row_nnz 512, chunk_nnz 256, group_nnz 0 (automatic: 256 except
+ * on small matrices), group_rows 32, warps_per_cta 1, persistent 0, pipeline 0, stage_rows 0. */
 void shiro_default_opts(shiro_opts* opts);
 
 /* Thread-local message of the last error. */

@@ -41,13 +41,13 @@ shiro_status resolve_opts(const shiro_opts* in, shiro_opts* o) {
     o->pipeline = in->pipeline;
     o->stage_rows = in->stage_rows;
   }
-  if (o->chunk_nnz < 32 || o->long_row_nnz < o->chunk_nnz || o->group_nnz < 1 ||
+  if (o->chunk_nnz < 32 || o->long_row_nnz < o->chunk_nnz || o->group_nnz < 0 ||
       o->group_rows < 1 || o->group_rows > 32 || o->warps_per_cta < 1 || o->warps_per_cta > 8 ||
       (o->stage_rows != 0 && o->stage_rows != 4 && o->stage_rows != 8 && o->stage_rows != 12 &&
        o->stage_rows != 16 && o->stage_rows != 32) ||
       o->pipeline < 0 || o->pipeline > 6)
     SHIRO_FAIL(SHIRO_ERR_INVALID_ARG,
-               "bad schedule options: need 32 <= chunk_nnz <= long_row_nnz, group_nnz >= 1, "
+               "bad schedule options: need 32 <= chunk_nnz <= long_row_nnz, group_nnz >= 0, "
                "1 <= group_rows <= 32, 1 <= warps_per_cta <= 8, "
                "stage_rows in {0, 4, 8, 12, 16, 32}, pipeline in {0, 1, 2, 3, 4, 5, 6}");
   return SHIRO_OK;
@@ -521,6 +521,11 @@ static shiro_status transpose_into(shiro_plan_s* P, const Shape& sh, const shiro
   return SHIRO_OK;
 }
 
+// Automatic row groups: at most kAutoGroupNnz nonzeros, and at most the short rows' nonzeros
+// over the resident warp slots (40 per SM for the 48-register gathers).
+constexpr int64_t kAutoGroupNnz = 256;
+constexpr int64_t kAutoWarpsPerSm = 40;
+
 shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s) {
   std::vector<Item> items;
   std::vector<int32_t> slot_lr;
@@ -529,9 +534,11 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
   const int64_t M = P->M;
   items.reserve((size_t)std::min<int64_t>(P->items_cap, M / 4 + 16));
   int32_t slot = 0;
+  int64_t long_nnz = 0;
   for (int64_t i = 0; i < M; ++i) {
     const int64_t len = rp[i + 1] - rp[i];
     if (len > o.long_row_nnz) {
+      long_nnz += len;
       const int32_t nch = (int32_t)((len + o.chunk_nnz - 1) / o.chunk_nnz);
       const int32_t lr = (int32_t)lrs.size();
       lrs.push_back({(int32_t)i, slot, nch, 0});
@@ -543,6 +550,17 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
     }
   }
   const int64_t n_chunk_items = (int64_t)items.size();
+  // group_nnz 0 (automatic): kAutoGroupNnz nonzeros, or fewer when the short rows' nonzeros spread
+  // over the warps the GPU keeps resident (SMs x kAutoWarpsPerSm) give less.  A small matrix then
+  // has an item for every warp slot, each a short span, instead of a few warps walking long spans
+  // one gather latency per step (Erdos-Renyi 4096 x 4096, 32.7 K nonzeros, N = 32: the SpMM
+  // launch took 49 us with groups of 256).  Rows are never split, so C does not change.
+  int64_t gnnz = o.group_nnz;
+  if (gnnz == 0) {
+    const int64_t slots = (int64_t)std::max(P->sm_count, 1) * kAutoWarpsPerSm;
+    gnnz = std::min<int64_t>(kAutoGroupNnz,
+                             std::max<int64_t>(1, (P->nnz - long_nnz + slots - 1) / slots));
+  }
   // Row groups never span two row blocks, so that every item belongs to one block (the fused
   // pack + SpMM releases a block's items once the block's rows are packed).
   const int32_t Pr = P->geo.Pr;
@@ -558,7 +576,7 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
     while (i < M && i < bend && cnt < o.group_rows) {
       const int64_t l = rp[i + 1] - rp[i];
       if (l > o.long_row_nnz) break;
-      if (cnt > 0 && nz + l > o.group_nnz) break;
+      if (cnt > 0 && nz + l > gnnz) break;
       nz += l;
       ++cnt;
       ++i;
@@ -685,7 +703,7 @@ void shiro_default_opts(shiro_opts* o) {
   // best or within 0.3% of the best candidate on every workload.
   o->long_row_nnz = 512;
   o->chunk_nnz = 256;
-  o->group_nnz = 256;
+  o->group_nnz = 0;  // automatic: 256, fewer for small matrices (build_schedule)
   o->group_rows = 32;
   o->warps_per_cta = 1;
   o->persistent = 0;

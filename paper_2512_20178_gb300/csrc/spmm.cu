@@ -167,7 +167,7 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
   // size, the largest rows decide whether splitting matters at all.
   const double avg = P->M ? (double)P->nnz / (double)P->M : 0.0;
   std::vector<shiro_opts> cands;
-  const int32_t groups[] = {128, 256, 512, 1024};
+  const int32_t groups[] = {0, 128, 256, 512, 1024};  // 0: automatic
   const int32_t chunks[] = {256, 512, 1024};
   const int32_t warps[] = {1, 2, 4};
   // Pipelines worth trying: register gathers (5), lane groups when rows are 128 or 256 bytes (3),
@@ -181,7 +181,7 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
                         (row_bytes == 128 || row_bytes == 256 || row_bytes == 512);
   const int32_t pipes[] = {5, 3, 4, 6};
   for (int32_t gn : groups) {
-    if (gn < avg / 2) continue;
+    if (gn && gn < avg / 2) continue;
     for (int32_t ch : chunks) {
       if (P->max_row_nnz <= ch && ch != 512) continue;
       for (int32_t w : warps) {

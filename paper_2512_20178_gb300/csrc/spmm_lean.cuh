@@ -39,6 +39,9 @@ constexpr int LEAN_MIN_BLOCKS = 20;
 // factor 1 / 2 / 4 / 8: FP32 N = 32 0.336 / 0.293 / 0.294 / 0.308; FP32 N = 64 0.370 / 0.381 /
 // 0.364; BF16 N = 64 0.359 / 0.356 / 0.316 / 0.366; BF16 N = 128 0.444 / 0.447 / 0.461; FP32 N =
 // 128 0.552 / 0.785 (spills).
+#ifndef SHIRO_LEAN_DYN_BF16V4
+#define SHIRO_LEAN_DYN_BF16V4 0
+#endif
 #ifndef SHIRO_LU_F32V1
 #define SHIRO_LU_F32V1 2
 #endif
@@ -63,7 +66,7 @@ struct LeanShape {
   // but BF16 rows of 256 bytes, measured slower with it (R-MAT 2^20, 4x4 tiles, ms, one item per
   // warp -> counter): FP32 N = 128 0.567 -> 0.554, N = 64 0.391 -> 0.371, N = 32 0.355 -> 0.331,
   // BF16 N = 256 0.815 -> 0.769 (R-MAT 2^22: 6.52 -> 6.16), BF16 N = 128 0.453 -> 0.474.
-  static constexpr bool DYN = !(std::is_same<TB, __nv_bfloat16>::value && VEC == 4);
+  static constexpr bool DYN = SHIRO_LEAN_DYN_BF16V4 || !(std::is_same<TB, __nv_bfloat16>::value && VEC == 4);
   static constexpr bool F32 = std::is_same<TB, float>::value;
   // BF16 rows of 512 bytes (eight FP32 accumulators per lane).
   static constexpr bool WIDE = std::is_same<TB, __nv_bfloat16>::value && VEC == 8;

@@ -38,6 +38,40 @@ def test_spmm_n_sweep(N):
     gu.check_spmm(A, B, C)
 
 
+@pytest.mark.parametrize("case", ["er4096_1d_local", "rmat14", "rmat14_bf16_n256"])
+def test_auto_groups_bit_identical(case):
+    """group_nnz 0 (automatic) cuts small matrices into more, shorter items than 256-nonzero
+    groups; rows are never split, so C and dA are bit-identical to the explicit 256 schedule."""
+    shiro = gu.lib()
+    flags = 0
+    dt = torch.float32
+    if case.startswith("er4096"):
+        A, Pr, N = synth.er(4096, 8, 1), 4, 32
+        flags = shiro.SHIRO_PLAN_LOCAL_DIAG
+    else:
+        A, Pr, N = synth.rmat(14, 16, 3), 4, 128
+        if case.endswith("bf16_n256"):
+            dt, N = torch.bfloat16, 256
+    P = gu.plan_of(A, Pr, Pr, flags)
+    assert P.info.opts.group_nnz == 0
+    d = gu.dev()
+    Bd = torch.from_numpy(synth.dense_normal(A.K, N, 5)).to(d).to(dt)
+    dC = torch.from_numpy(synth.dense_normal(A.M, N, 6)).to(d).to(dt)
+    out = {}
+    for gn in (0, 256):
+        P.reschedule(group_nnz=gn)
+        Bp = P.pack(Bd)
+        C = P.spmm(Bp, B=Bd)
+        dA = P.sddmm(dC, Bp, B=Bd)
+        torch.cuda.synchronize()
+        P.check()
+        out[gn] = (P.info.n_items, C, dA)
+    assert out[0][0] > out[256][0], "automatic groups should give more items on a small matrix"
+    assert torch.equal(out[0][1], out[256][1]) and torch.equal(out[0][2], out[256][2])
+    if dt == torch.float32:
+        gu.check_spmm(A, Bd.cpu().numpy(), out[0][1])
+
+
 @pytest.mark.parametrize("name", ["er4096_2d", "er4096_1d_local", "ragged", "more_blocks",
                                   "empty_rows", "rmat14_default"])
 def test_spmm_cases(name):

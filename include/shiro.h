@@ -101,10 +101,11 @@ typedef struct {
                             from a counter, those of the other pipelines stride over them */
   int32_t pipeline;      /* How the gathered B rows reach the accumulators (every pipeline sums
                             a row's nonzeros in the same order, except 3):
-                            0: automatic -- 6 for FP32/BF16 rows of 128 to 512 bytes (in its
-                               counter form except for BF16 rows of 256 bytes; 5 in persistent
-                               mode), 4 for FP32/BF16 rows of 1-2 KB, else 5 (the fastest
-                               measured for each row size);
+                            0: automatic -- 7 for BF16 rows of 512 bytes, 6 for the other
+                               FP32/BF16 rows of 128 to 512 bytes (in its counter form except
+                               for BF16 rows of 256 bytes; 5 in persistent mode), 4 for FP32/BF16
+                               rows of 1-2 KB, else 5 (the fastest measured for each row size;
+                               shiro_pack_spmm runs rows of 512 bytes as one fused launch);
                             1: staged through shared memory by per-lane asynchronous copies, two
                                stages per warp;
                             2: staged by one TMA bulk copy per row, two stages per warp (rows of
@@ -120,7 +121,11 @@ typedef struct {
                                128-512 bytes; else 5): 2-warp CTAs, 40 warps per SM, the next
                                batch's (index, value) pairs copied into shared memory
                                asynchronously; warps_per_cta does not apply; one item per warp,
-                               or with persistent set, items taken from a counter in the plan.
+                               or with persistent set, items taken from a counter in the plan;
+                            7: FP32/BF16 rows of 512 bytes moved into shared memory by TMA gathers
+                               of four packed rows (tile::gather4, one tensor map over the packed
+                               buffer), eight gathers in flight per warp, items from a counter
+                               (not LOCAL_DIAG plans, else as 5).
                             shiro_sddmm reads 5 and 6 too (see there). */
   int32_t stage_rows;    /* pipeline 1: rows per stage, 8, 16 or 32 (0 = the largest that keeps a
                             stage within 16 KB); pipeline 4: ring depth, 16 or 32 for 256-byte

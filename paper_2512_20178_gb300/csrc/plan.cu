@@ -45,11 +45,11 @@ shiro_status resolve_opts(const shiro_opts* in, shiro_opts* o) {
       o->group_rows < 1 || o->group_rows > 32 || o->warps_per_cta < 1 || o->warps_per_cta > 8 ||
       (o->stage_rows != 0 && o->stage_rows != 4 && o->stage_rows != 8 && o->stage_rows != 12 &&
        o->stage_rows != 16 && o->stage_rows != 32) ||
-      o->pipeline < 0 || o->pipeline > 6)
+      o->pipeline < 0 || o->pipeline > 7)
     SHIRO_FAIL(SHIRO_ERR_INVALID_ARG,
                "bad schedule options: need 32 <= chunk_nnz <= long_row_nnz, group_nnz >= 0, "
                "1 <= group_rows <= 32, 1 <= warps_per_cta <= 8, "
-               "stage_rows in {0, 4, 8, 12, 16, 32}, pipeline in {0, 1, 2, 3, 4, 5, 6}");
+               "stage_rows in {0, 4, 8, 12, 16, 32}, pipeline in {0, 1, 2, 3, 4, 5, 6, 7}");
   return SHIRO_OK;
 }
 

@@ -172,14 +172,16 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
   const int32_t warps[] = {1, 2, 4};
   // Pipelines worth trying: register gathers (5), lane groups when rows are 128 or 256 bytes (3),
   // the per-lane copy ring for rows of 512 bytes to 2 KB (4), lean register gathers for rows of
-  // 128 to 512 bytes (6; in persistent mode their counter form).
+  // 128 to 512 bytes (6; in persistent mode their counter form), the TMA gather4 ring for rows of
+  // 512 bytes (7).
   const int64_t row_bytes = (int64_t)N * (int64_t)dtype_size(dt);
   const bool narrow = dt != SHIRO_F64 && (row_bytes == 128 || row_bytes == 256);
   const bool ringable = dt != SHIRO_F64 && (row_bytes == 512 || row_bytes == 1024 ||
                                             row_bytes == 2048);
   const bool leanable = dt != SHIRO_F64 &&
                         (row_bytes == 128 || row_bytes == 256 || row_bytes == 512);
-  const int32_t pipes[] = {5, 3, 4, 6};
+  const bool g4able = dt != SHIRO_F64 && row_bytes == 512 && !(P->flags & SHIRO_PLAN_LOCAL_DIAG);
+  const int32_t pipes[] = {5, 3, 4, 6, 7};
   for (int32_t gn : groups) {
     if (gn && gn < avg / 2) continue;
     for (int32_t ch : chunks) {
@@ -189,6 +191,7 @@ shiro_status shiro_autotune(shiro_plan_t P, const void* Bpack, int64_t ldp, cons
           if (pipe == 3 && !narrow) continue;
           if (pipe == 4 && !ringable) continue;
           if (pipe == 6 && (!leanable || w != 1)) continue;  // lean CTAs are always 2 warps
+          if (pipe == 7 && (!g4able || w != 1)) continue;    // gather4 CTAs have a fixed shape
           shiro_opts o = start;
           o.group_nnz = gn;
           o.group_rows = 32;

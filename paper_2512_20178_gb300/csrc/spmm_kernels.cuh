@@ -345,6 +345,7 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Bas
 #include "spmm_grouped.cuh"
 #include "spmm_ring.cuh"
 #include "spmm_lean.cuh"
+#include "spmm_gather4.cuh"
 
 namespace shiro {
 
@@ -645,6 +646,50 @@ static shiro_status launch_lean(const shiro_plan_s* P, const SpmmParams<TV, TB>&
   return SHIRO_OK;
 }
 
+// Rows of 512 bytes gathered by TMA gather4 into shared memory (pipeline 7): not LOCAL_DIAG
+// (every row comes from the packed buffer), the buffer 16-byte aligned with a row stride of a
+// multiple of 16 bytes, at least one packed row.
+template <typename TV, typename TB, int VEC>
+static bool g4_ok(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm) {
+  return !(P->flags & SHIRO_PLAN_LOCAL_DIAG) && P->packed_rows > 0 &&
+         (int64_t)prm.N * (int64_t)sizeof(TB) == 512 && ((uintptr_t)prm.Bpack % 16) == 0 &&
+         ((uint64_t)prm.ldp * sizeof(TB)) % 16 == 0 && tensor_map_encoder() != nullptr;
+}
+
+template <typename TV, typename TB, int VEC>
+static shiro_status launch_g4(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                              cudaStream_t s) {
+  constexpr int D = G4Shape<TB>::D, W = G4Shape<TB>::W;
+  using L = G4Layout<TV, D>;
+  auto kern = k_spmm_g4<TV, TB, VEC, D, W>;
+  if (prm.n_items <= 0) return SHIRO_OK;
+  if (prm.n_items > INT32_MAX) SHIRO_FAIL(SHIRO_ERR_UNSUPPORTED, "too many work items");
+  // The packed buffer as R rows of 128 32-bit words, one row per box.
+  CUtensorMap tm;
+  const cuuint64_t gdim[2] = {128, (cuuint64_t)P->packed_rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)prm.ldp * sizeof(TB)};
+  const cuuint32_t box[2] = {128, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = tensor_map_encoder()(
+      &tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<TB*>(prm.Bpack), gdim, gstride, box,
+      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) SHIRO_FAIL(SHIRO_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  const int smem = W * L::WARP;
+  SHIRO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  SHIRO_CUDA(blocks_per_sm(&per_sm, kern, W * 32, (size_t)smem));
+  const int64_t grid = std::min<int64_t>((prm.n_items + W - 1) / W,
+                                         (int64_t)std::max(per_sm, 1) * P->sm_count);
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.work = P->d_status + 2;
+  SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));
+  kern<<<(unsigned)grid, W * 32, smem, s>>>(q, tm);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
 template <typename TV, typename TB, int VEC, int NCH, bool MASKED>
 static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
                                cudaStream_t s) {
@@ -657,6 +702,16 @@ static shiro_status launch_one(const shiro_plan_s* P, const SpmmParams<TV, TB>& 
                   (ROW & (ROW - 1)) == 0) {
       if (P->opts.pipeline == 4 || (P->opts.pipeline == 0 && ROW >= 1024))
         return launch_lring<TV, TB, VEC, NCH>(P, prm, s);
+    }
+    // TMA gather4 ring (pipeline 7), and with pipeline 0 for BF16 rows of 512 bytes outside
+    // persistent mode (measured faster there: R-MAT 2^20 0.824 -> 0.771 ms, R-MAT 2^22 avg degree
+    // 32 6.00 -> 5.75 ms; FP32 rows of 512 bytes stay on the 48-register gathers, 0.552 against
+    // 0.656).
+    if constexpr (!std::is_same<TB, double>::value && NCH == 1 && ROW == 512) {
+      const bool automatic = std::is_same<TB, __nv_bfloat16>::value && P->opts.pipeline == 0 &&
+                             !P->opts.persistent;
+      if ((P->opts.pipeline == 7 || automatic) && g4_ok<TV, TB, VEC>(P, prm))
+        return launch_g4<TV, TB, VEC>(P, prm, s);
     }
     // Lean register gathers (pipeline 6; 48 registers, 2-warp CTAs; persistent mode takes items
     // from a counter): with pipeline 0 (automatic) rows of 128 to 512 bytes take them outside

@@ -74,7 +74,7 @@ def test_host_validation(lib):
     # Pipelines 0-6 and the listed ring / stage depths are accepted, others rejected.
     for pipe in range(7):
         assert _ws(lib, 10, 10, 5, 2, 2, pipeline=pipe)[0] == 0, pipe
-    assert _ws(lib, 10, 10, 5, 2, 2, pipeline=7)[0] == 1
+    assert _ws(lib, 10, 10, 5, 2, 2, pipeline=8)[0] == 1
     assert _ws(lib, 10, 10, 5, 2, 2, pipeline=-1)[0] == 1
     for rows in (0, 4, 8, 12, 16, 32):
         assert _ws(lib, 10, 10, 5, 2, 2, pipeline=4, stage_rows=rows)[0] == 0, rows

@@ -32,7 +32,7 @@ def test_spmm_kernel_names():
     assert bench.spmm_kernel(128, 4) == "k_spmm_lean_dyn"    # FP32 N = 128, 512-byte rows
     assert bench.spmm_kernel(32, 4) == "k_spmm_lean_dyn"     # 128-byte rows
     assert bench.spmm_kernel(128, 2) == "k_spmm_lean"        # BF16 256-byte rows: one item per warp
-    assert bench.spmm_kernel(256, 2) == "k_spmm_lean_dyn"
+    assert bench.spmm_kernel(256, 2) == "k_spmm_g4"          # BF16 512-byte rows: TMA gather4
     assert bench.spmm_kernel(256, 4) == "k_spmm_lring"       # 1 KB rows
     assert bench.spmm_kernel(16, 4) == "k_spmm"
 

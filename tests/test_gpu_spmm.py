@@ -211,8 +211,8 @@ def test_full_size_rmat20_sampled_rows(rmat20):
                                   "hub", "narrow_local_diag", "narrow_accumulate", "narrow_hub"])
 def test_pipelines_bit_identical(case):
     """Register gathers (64- and 48-register forms), per-lane async copies and TMA bulk copies in
-    two stages, and the per-lane copy ring sum every row in the same order, so all pipelines give
-    bit-identical C (and each passes the oracle bound)."""
+    two stages, the per-lane copy ring and the TMA gather4 ring (rows of 512 bytes) sum every row
+    in the same order, so all pipelines give bit-identical C (and each passes the oracle bound)."""
     shiro = gu.lib()
     flags, vdt, dt, acc = 0, torch.float32, torch.float32, False
     A, N = synth.rmat(13, 12, 131), 128
@@ -247,7 +247,7 @@ def test_pipelines_bit_identical(case):
     # the per-lane copy ring at each compiled depth (and persistent), the 48-register gathers
     # (and their persistent fallback).
     runs = [(5, 0, 0), (1, 0, 0), (2, 0, 0), (0, 0, 0), (4, 0, 0), (4, 4, 0), (4, 8, 0),
-            (4, 12, 0), (4, 16, 1), (4, 32, 0), (6, 0, 0), (6, 0, 1)]
+            (4, 12, 0), (4, 16, 1), (4, 32, 0), (6, 0, 0), (6, 0, 1), (7, 0, 0)]
     for pipe, rows, pers in runs:
         opts = shiro.make_opts(pipeline=pipe, long_row_nnz=128, chunk_nnz=64, group_nnz=256,
                                warps_per_cta=2, stage_rows=rows, persistent=pers)

@@ -164,6 +164,13 @@ def sddmm_bytes(M, nnz, R, N, sz):
     return nnz * 8 + M * N * sz + R * N * sz + nnz * 4
 
 
+def bwd_bytes(K, nnz, RT, N, sz, nzc):
+    """Algorithmic bytes of the one-launch backward over A^T (K rows, RT packed dC rows): the pack
+    of dC, the SpMM of A^T over the packed rows (writing dB), one B row per non-empty row of A^T
+    (nzc of them) and the dA values."""
+    return pack_bytes(RT, N, sz) + spmm_bytes(K, nnz, RT, N, sz) + nzc * N * sz + nnz * 4
+
+
 def step_bytes(M, nnz, R, N, sz):
     return spmm_bytes(M, nnz, R, N, sz), pack_bytes(R, N, sz)
 
@@ -710,12 +717,24 @@ def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, st
         db_pack = run(lambda: PT.pack(G, out=Gp))
         db_ms = run(lambda: PT.pack_spmm(G, Bpack=Gp, out=dB, scratch=sT))
         da_ms = run(lambda: P.sddmm(G, Bp, out=dA))
+        # The backward as the autograd wrapper runs it: one launch for dB and dA (B given).
+        bwd_ms = run(lambda: shiro.spmm_backward(P, PT, G, Bp, B=Bd, scratch=sT, dCpack=Gp,
+                                                 dB=dB, dA=dA))
         wname = workload_name(args.scale, args.deg, N, args.tiles, "f32")
         sd = frac_entry(sddmm_bytes(A.M, A.nnz, R, N, 4), da_ms, peak)
         sd["kernel"] = "k_sddmm_grp"
         sd["traffic"] = traffic_from_profile("k_sddmm_grp", wname)
+        nzc = int(np.count_nonzero(np.bincount(A.col, minlength=A.K)))
+        one = frac_entry(bwd_bytes(A.K, A.nnz, RT, N, 4, nzc), bwd_ms, peak)
+        one["kernel"] = "k_spmm_lean_bwd"
+        one["traffic"] = traffic_from_profile("k_spmm_lean_bwd", wname)
+        one["bytes_definition"] = ("pack 2*RT*N*4 + RT*4, SpMM of A^T (K+1)*8 + nnz*8 + RT*N*4 + "
+                                   "K*N*4, B rows nzc*N*4, dA nnz*4")
         out["backward"] = {
-            "workload": wname, "fwd_ms": fwd_ms, "fwd_bwd_ms": fwd_ms + db_ms + da_ms,
+            "workload": wname, "fwd_ms": fwd_ms, "fwd_bwd_ms": fwd_ms + bwd_ms,
+            "bwd_one_launch": one,
+            "two_calls": {"fwd_bwd_ms": fwd_ms + db_ms + da_ms, "bwd_ms": db_ms + da_ms,
+                          "what": "shiro_pack_spmm on the transposed plan, then shiro_sddmm"},
             "dB_step_ms": db_ms, "dB_spmm": frac_entry(spmm_bytes(A.K, A.nnz, RT, N, 4), db_spmm, peak),
             "dB_pack": frac_entry(pack_bytes(RT, N, 4), db_pack, peak),
             "dB_step_GBps_spmm_bytes": gbps(spmm_bytes(A.K, A.nnz, RT, N, 4), db_ms),
@@ -845,7 +864,7 @@ def form_gcn(dev, stream, peak, reps, scale=20, deg=16, N=128, F=256, seed=4, ti
     gives dX and dW through torch and dH (A_hat^T dY: pack + SpMM on the transposed plan) and the
     gradient of A_hat's values (SDDMM) through the library.  Loss <G, Y> with a fixed G."""
     import torch
-    from paper_2512_20178_gb300 import autograd, synth
+    from paper_2512_20178_gb300 import autograd, shiro, synth
     A = synth.gcn_normalized(scale, deg, seed)
     rp = torch.from_numpy(A.rowptr).to(dev)
     col = torch.from_numpy(A.col).to(dev)
@@ -885,6 +904,9 @@ def form_gcn(dev, stream, peak, reps, scale=20, deg=16, N=128, F=256, seed=4, ti
         dh_pack = timed(lambda: PT.pack(G, out=Gp), stream, reps)
         dA = torch.empty(A.nnz, device=dev)
         da_ms = timed(lambda: P.sddmm(G, Hp, out=dA), stream, reps)
+        bwd_ms = timed(lambda: shiro.spmm_backward(P, PT, G, Hp, B=H, scratch=scT, dCpack=Gp,
+                                                   dB=dH, dA=dA), stream, reps)
+        nzc = int(np.count_nonzero(np.bincount(A.col, minlength=A.K)))
     fwd_ms = timed(fwd, stream, reps)
     ms = timed(fwd_bwd, stream, reps)
     return {"workload": f"gcn_rmat{scale}_deg{deg}_F{F}_N{N}_{tiles}x{tiles}_f32", "M": A.M,
@@ -895,8 +917,10 @@ def form_gcn(dev, stream, peak, reps, scale=20, deg=16, N=128, F=256, seed=4, ti
                            "pack": frac_entry(pack_bytes(R, N, 4), pack_ms, peak)},
             "sparse_bwd": {"dH_spmm": frac_entry(spmm_bytes(A.K, A.nnz, RT, N, 4), dh_spmm, peak),
                            "dH_pack": frac_entry(pack_bytes(RT, N, 4), dh_pack, peak),
-                           "dA_sddmm": frac_entry(sddmm_bytes(A.M, A.nnz, R, N, 4), da_ms, peak)},
-            "sparse_ms": spmm_ms + pack_ms + dh_spmm + dh_pack + da_ms,
+                           "dA_sddmm": frac_entry(sddmm_bytes(A.M, A.nnz, R, N, 4), da_ms, peak),
+                           "dH_dA_one_launch": frac_entry(bwd_bytes(A.K, A.nnz, RT, N, 4, nzc),
+                                                          bwd_ms, peak)},
+            "sparse_ms": spmm_ms + pack_ms + bwd_ms,
             "sparse_fwd_gflops": 2.0 * A.nnz * N / (spmm_ms * 1e-3) / 1e9,
             "what": "fwd + bwd through torch.autograd: X W and the dense gradients in torch (FP32), "
                     "pack + SpMM, dH and dA_hat in the library"}

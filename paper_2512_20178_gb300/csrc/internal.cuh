@@ -187,5 +187,12 @@ inline cudaError_t blocks_per_sm(int* per_sm, K kern, int threads, size_t smem) 
 shiro_status launch_pack_spmm(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N,
                               shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,
                               uint32_t flags, void* scratch, size_t scratch_bytes, cudaStream_t s);
+// dB (through the TRANSPOSE plan planT, as launch_pack_spmm) and dA of `plan` in one launch where
+// the row shape and operands allow; *done = false (nothing launched) otherwise.
+shiro_status launch_backward_one(const shiro_plan_s* plan, const shiro_plan_s* planT,
+                                 const void* dC, int64_t lddc, const void* B, int64_t ldb,
+                                 int32_t N, shiro_dtype dt, void* dCpack, int64_t lddp, void* dB,
+                                 int64_t lddb, void* dA, void* scratch, size_t scratch_bytes,
+                                 cudaStream_t s, bool* done);
 
 }  // namespace shiro

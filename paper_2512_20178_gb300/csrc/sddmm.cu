@@ -404,6 +404,12 @@ shiro_status shiro_spmm_backward(shiro_plan_t plan, shiro_plan_t planT, const vo
       SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "dB needs the TRANSPOSE plan of the same matrix");
     if (planT->M != plan->K || planT->K != plan->M || planT->nnz != plan->nnz)
       SHIRO_FAIL(SHIRO_ERR_INVALID_ARG, "planT is not the transpose of plan");
+    if (dA) {
+      bool done = false;
+      SHIRO_TRY(launch_backward_one(plan, planT, dC, lddc, B, ldb, N, dt, dCpack, lddp, dB, lddb,
+                                    dA, scratch, scratch_bytes, s, &done));
+      if (done) return SHIRO_OK;
+    }
     SHIRO_TRY(launch_pack_spmm(planT, dC, lddc, N, dt, dCpack, lddp, dB, lddb, 0, scratch,
                                scratch_bytes, s));
   }

@@ -61,6 +61,14 @@ SHIRO_FUSED_TYPED(spmm_fused_f32)
 SHIRO_FUSED_TYPED(spmm_fused_bf16)
 SHIRO_FUSED_TYPED(spmm_fused_f64)
 #undef SHIRO_FUSED_TYPED
+#define SHIRO_BWD_TYPED(name)                                                                    \
+  shiro_status name(const shiro_plan_s* PT, const void* dC, int64_t lddc, int32_t N,             \
+                    shiro_dtype dt, void* dCpack, int64_t lddp, void* dB, int64_t lddb,          \
+                    const void* B, int64_t ldb, void* dA, void* scratch, cudaStream_t s,         \
+                    bool* done);
+SHIRO_BWD_TYPED(spmm_bwd_f32)
+SHIRO_BWD_TYPED(spmm_bwd_bf16)
+#undef SHIRO_BWD_TYPED
 
 size_t spmm_scratch_bytes(const shiro_plan_s* P, int32_t N, shiro_dtype dt) {
   if (!P->n_slots) return 0;
@@ -125,6 +133,30 @@ shiro_status launch_pack_spmm(const shiro_plan_s* plan, const void* B, int64_t l
   // Other row shapes and schedules: the two launches, same results.
   SHIRO_TRY(launch_pack(plan, B, ldb, N, dt, Bpack, ldp, s));
   return launch_spmm(plan, Bpack, ldp, B, ldb, N, dt, C, ldc, flags, scratch, scratch_bytes, s);
+}
+
+shiro_status launch_backward_one(const shiro_plan_s* plan, const shiro_plan_s* planT,
+                                 const void* dC, int64_t lddc, const void* B, int64_t ldb,
+                                 int32_t N, shiro_dtype dt, void* dCpack, int64_t lddp, void* dB,
+                                 int64_t lddb, void* dA, void* scratch, size_t scratch_bytes,
+                                 cudaStream_t s, bool* done) {
+  *done = false;
+  // Only well-formed calls with work to do; anything else goes the two-call way, which reports
+  // the error or handles the empty case.
+  if (!B || !dC || !dB || !dA || N <= 0 || plan->nnz == 0 || planT->M == 0) return SHIRO_OK;
+  if (plan->vdt != SHIRO_F32 || planT->vdt != SHIRO_F32) return SHIRO_OK;
+  if (dt != SHIRO_F32 && dt != SHIRO_BF16) return SHIRO_OK;
+  if (lddc < N || lddp < N || lddb < N || ldb < N) return SHIRO_OK;
+  if (lddp > (int64_t)UINT32_MAX || lddc > (int64_t)UINT32_MAX || ldb > (int64_t)UINT32_MAX)
+    return SHIRO_OK;
+  if (!dCpack && planT->packed_rows > 0) return SHIRO_OK;
+  const size_t need = spmm_scratch_bytes(planT, N, dt);
+  if (need && (!scratch || scratch_bytes < need)) return SHIRO_OK;
+  if (dt == SHIRO_F32)
+    return spmm_bwd_f32(planT, dC, lddc, N, dt, dCpack, lddp, dB, lddb, B, ldb, dA, scratch, s,
+                        done);
+  return spmm_bwd_bf16(planT, dC, lddc, N, dt, dCpack, lddp, dB, lddb, B, ldb, dA, scratch, s,
+                       done);
 }
 
 }  // namespace shiro

@@ -16,4 +16,12 @@ shiro_status spmm_fused_bf16(const shiro_plan_s* P, const void* B, int64_t ldb, 
                                       fused);
 }
 
+shiro_status spmm_bwd_bf16(const shiro_plan_s* PT, const void* dC, int64_t lddc, int32_t N,
+                          shiro_dtype dt, void* dCpack, int64_t lddp, void* dB, int64_t lddb,
+                          const void* B, int64_t ldb, void* dA, void* scratch, cudaStream_t s,
+                          bool* done) {
+  return spmm_bwd_typed<float, __nv_bfloat16>(PT, dC, lddc, N, dt, dCpack, lddp, dB, lddb, B, ldb, dA,
+                                    scratch, s, done);
+}
+
 }  // namespace shiro

@@ -346,6 +346,7 @@ __device__ __forceinline__ void run_chunk(const SpmmParams<TV, TB>& p, const Bas
 #include "spmm_ring.cuh"
 #include "spmm_lean.cuh"
 #include "spmm_gather4.cuh"
+#include "spmm_bwd.cuh"
 
 namespace shiro {
 
@@ -898,6 +899,63 @@ static shiro_status spmm_fused_typed(const shiro_plan_s* P, const void* B, int64
     }
     *fused = false;
     return SHIRO_OK;
+  }
+}
+
+template <typename TV, typename TB, int VEC>
+static shiro_status launch_lean_bwd(const shiro_plan_s* P, const SpmmParams<TV, TB>& prm,
+                                    const FusedParams<TB>& f, const SdParams<TB>& sd,
+                                    cudaStream_t s) {
+  constexpr int U = LeanShape<TB, VEC>::WIDE ? SHIRO_LEAN_UW : Occupancy<VEC, 1, TB>::U;
+  const bool local = P->flags & SHIRO_PLAN_LOCAL_DIAG;
+  auto kern = local ? k_spmm_lean_bwd<TV, TB, VEC, U, true> : k_spmm_lean_bwd<TV, TB, VEC, U, false>;
+  if (f.n_seq <= 0) return SHIRO_OK;
+  int per_sm = 0;
+  SHIRO_CUDA(blocks_per_sm(&per_sm, kern, 64, 0));
+  const int64_t grid = std::min<int64_t>(((int64_t)f.n_seq + 1) / 2,
+                                         (int64_t)std::max(per_sm, 1) * P->sm_count);
+  SpmmParams<TV, TB> q = prm;
+  q.n_chunk_items = P->n_slots;
+  q.work = P->d_status + 2;
+  SHIRO_CUDA(cudaMemsetAsync(q.work, 0, sizeof(int32_t), s));
+  SHIRO_CUDA(cudaMemsetAsync(f.done, 0, sizeof(int32_t) * (size_t)std::max(P->geo.Pr, 1), s));
+  kern<<<(unsigned)grid, 64, 0, s>>>(q, f, sd);
+  SHIRO_CUDA(cudaGetLastError());
+  return SHIRO_OK;
+}
+
+// The backward in one launch (k_spmm_lean_bwd) on the TRANSPOSE plan PT: dCpack and dB as
+// spmm_fused_typed(PT, dC, ...) computes them, plus dA (A's nonzero order) from the same gathers
+// and B.  For the shapes and schedules spmm_fused_typed runs in one launch, with B aligned to 16
+// bytes; *done = false (nothing launched) otherwise.
+template <typename TV, typename TB>
+static shiro_status spmm_bwd_typed(const shiro_plan_s* PT, const void* dC, int64_t lddc,
+                                   int32_t N, shiro_dtype dt, void* dCpack, int64_t lddp,
+                                   void* dB, int64_t lddb, const void* B, int64_t ldb, void* dA,
+                                   void* scratch, cudaStream_t s, bool* done) {
+  using TA = typename AccOf<TB>::T;
+  *done = false;
+  if constexpr (std::is_same<TB, double>::value) {
+    return SHIRO_OK;
+  } else {
+    if (PT->opts.persistent || (PT->opts.pipeline != 0 && PT->opts.pipeline != 6)) return SHIRO_OK;
+    if (PT->n_fseq > INT32_MAX || !PT->d_perm) return SHIRO_OK;
+    const size_t esz = dtype_size(dt);
+    if ((int64_t)N * (int64_t)esz != 512) return SHIRO_OK;
+    const int v16 = (int)(16 / esz);
+    if (!(aligned(dCpack, lddp, esz, v16) && aligned(dB, lddb, sizeof(TA), v16) &&
+          aligned(dC, lddc, esz, v16) && aligned(B, ldb, esz, v16)))
+      return SHIRO_OK;
+    const SpmmParams<TV, TB> prm =
+        make_params<TV, TB>(PT, dCpack, lddp, dC, lddc, N, dt, dB, lddb, 0, scratch);
+    FusedParams<TB> f{PT->d_fseq, (int32_t)PT->n_fseq, PT->d_pchunk, PT->d_blk_need,
+                      PT->d_blk_done, PT->d_pack_src, (TB*)dCpack, PT->geo};
+    SdParams<TB> sd{(const TB*)B, (uint32_t)ldb, (float*)dA, PT->d_perm};
+    *done = true;
+    if constexpr (std::is_same<TB, float>::value)
+      return launch_lean_bwd<TV, TB, 4>(PT, prm, f, sd, s);
+    else
+      return launch_lean_bwd<TV, TB, 8>(PT, prm, f, sd, s);
   }
 }
 

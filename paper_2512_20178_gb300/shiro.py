@@ -418,14 +418,22 @@ class Plan:
 
 
 def spmm_backward(plan: Plan, planT: Plan, dC, Bpack, B=None, want_dB=True, want_dA=True,
-                  scratch=None, stream=None):
-    """dB = A^T dC (through planT) and dA on A's pattern, in one C call."""
+                  scratch=None, stream=None, dCpack=None, dB=None, dA=None):
+    """dB = A^T dC (through planT) and dA on A's pattern, in one C call (one launch for rows of
+    512 bytes when B is given).  dCpack, dB and dA may be passed preallocated."""
     N = dC.shape[1]
     dev = dC.device
     acc = _ACC[dC.dtype]
-    dCpack = torch.empty((planT.info.packed_rows, N), dtype=dC.dtype, device=dev) if want_dB else None
-    dB = torch.empty((planT.info.M, N), dtype=acc, device=dev) if want_dB else None
-    dA = torch.empty(plan.info.nnz, dtype=acc, device=dev) if want_dA else None
+    if want_dB and dCpack is None:
+        dCpack = torch.empty((planT.info.packed_rows, N), dtype=dC.dtype, device=dev)
+    if want_dB and dB is None:
+        dB = torch.empty((planT.info.M, N), dtype=acc, device=dev)
+    if want_dA and dA is None:
+        dA = torch.empty(plan.info.nnz, dtype=acc, device=dev)
+    if not want_dB:
+        dCpack = dB = None
+    if not want_dA:
+        dA = None
     if scratch is None and want_dB:
         scratch = planT.new_scratch(N, dC.dtype)
     sb = scratch.numel() if scratch is not None else 0

@@ -24,8 +24,63 @@ struct SdParams {
 };
 
 #ifndef SHIRO_BWD_MINB
-#define SHIRO_BWD_MINB 18  // 2-warp CTAs per SM (56 registers)
+// 2-warp CTAs per SM.  Backward ms (R-MAT 2^20, FP32 N = 128 / BF16 N = 256 degree 32) at 16
+// (64 registers) 1.178 / 2.472, 18 (56) 1.132 / 2.475, 20 (48, 80-100 bytes spilled) 1.171 /
+// 2.523.
+#define SHIRO_BWD_MINB 18
 #endif
+
+// Measured on R-MAT 2^20 (4x4 tiles), backward ms FP32 N = 128 / BF16 N = 256 (degree 32), with
+// (hint, group prefetch) = (0, 1) 1.138 / 2.470, (1, 1) 1.128 / 2.472, (1, 0) 1.125 / 2.480,
+// (0, 0) 1.130 / 2.481: all within noise.  Tried and slower: a register copy of the next row's B
+// row loaded a row ahead (1.18 / 2.53: spills), and dA written in A^T's order with a separate
+// scatter pass to A's order (1.18 / 2.68).
+#ifndef SHIRO_BWD_HINT
+#define SHIRO_BWD_HINT 1  // evict-first L2 policy on the streamed pattern, nonzero ids and B rows
+#endif
+#ifndef SHIRO_BWD_GROUP_PF
+#define SHIRO_BWD_GROUP_PF 1  // a group's B rows brought into L2 when the group starts
+#endif
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+
+// cp.async of BYTES (4 or 8) with an L2 cache policy.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_hint(uint32_t smem, const void* gmem, uint64_t pol) {
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;\n" ::"r"(smem),
+               "l"(gmem), "n"(BYTES), "l"(pol)
+               : "memory");
+}
+
+// The lane's 16-byte slice of a B row as floats.  B's rows are read once per row of A^T (a long
+// row's chunks read it again, mostly from L2); with SHIRO_BWD_HINT the read carries an
+// evict-first L2 policy so that it displaces fewer of the gathered dC rows.
+template <typename TB, int VEC>
+__device__ __forceinline__ void load_b_row(const TB* p, float (&f)[VEC]) {
+  static_assert(VEC * sizeof(TB) == 16, "16-byte slices");
+  if constexpr (SHIRO_BWD_HINT) {
+    uint32_t w[4];
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;\n"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                 : "l"(p), "l"(evict_first_policy()));
+    if constexpr (std::is_same<TB, float>::value) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) f[v] = __uint_as_float(w[v]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        f[2 * k] = bf16_lo(w[k]);
+        f[2 * k + 1] = bf16_hi(w[k]);
+      }
+    }
+  } else {
+    load_vec<TB, VEC, true>(p, f);
+  }
+}
 
 // Sum over the lane's VEC elements of dC * B: two partial sums (even and odd elements, paired
 // FMAs), added at the end.
@@ -145,8 +200,8 @@ __device__ __forceinline__ void bwd_batch(const SpmmParams<TV, TB>& p, const SdP
             // The next nonzero's row: the first lane whose row ends beyond this position.
             const unsigned nx = __ballot_sync(0xffffffffu, rel > pos);
             if (nx)
-              load_vec<TB, VEC, true>(sd.B + (uint64_t)(uint32_t)(r0 + __ffs(nx) - 1) * sd.ldb +
-                                          lane * VEC, bj);
+              load_b_row<TB, VEC>(sd.B + (uint64_t)(uint32_t)(r0 + __ffs(nx) - 1) * sd.ldb +
+                                      lane * VEC, bj);
           }
         }
       }
@@ -169,12 +224,12 @@ __device__ __forceinline__ void bwd_span(const SpmmParams<TV, TB>& p, const SdPa
   const unsigned ne = __ballot_sync(0xffffffffu, rel > 0);
   const int32_t row = ne ? r0 + __ffs(ne) - 1 : r0;
   // The group's later rows are needed one after another: bring their B rows into L2 now.
-  if (p.pf_bytes && rel > 0 && r0 + lane != row)
+  if (SHIRO_BWD_GROUP_PF && p.pf_bytes && rel > 0 && r0 + lane != row)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
                      sd.B + (uint64_t)(uint32_t)(r0 + lane) * sd.ldb),
                  "r"(p.pf_bytes));
   float bj[VEC];
-  load_vec<TB, VEC, true>(sd.B + (uint64_t)(uint32_t)row * sd.ldb + lane * VEC, bj);
+  load_b_row<TB, VEC>(sd.B + (uint64_t)(uint32_t)row * sd.ldb + lane * VEC, bj);
   __syncwarp();
   if (lane < total) {
     Pair<TV> pr;
@@ -192,11 +247,20 @@ __device__ __forceinline__ void bwd_span(const SpmmParams<TV, TB>& p, const SdPa
     __syncwarp();
     if (off + 32 + lane < total) {
       const uint32_t d = (uint32_t)__cvta_generic_to_shared(nxt + lane);
-      cp_async<4>(d, p.remap + base + off + 32 + lane);
-      cp_async<(int)sizeof(TV)>(d + (uint32_t)offsetof(Pair<TV>, val),
-                                p.val + base + off + 32 + lane);
-      cp_async<8>((uint32_t)__cvta_generic_to_shared(spm + (h ^ 1) * 32 + lane),
-                  sd.perm + base + off + 32 + lane);
+      const uint32_t dm = (uint32_t)__cvta_generic_to_shared(spm + (h ^ 1) * 32 + lane);
+      if constexpr (SHIRO_BWD_HINT) {
+        // The pattern and the nonzero ids are read once.
+        const uint64_t pol = evict_first_policy();
+        cp_async_hint<4>(d, p.remap + base + off + 32 + lane, pol);
+        cp_async_hint<(int)sizeof(TV)>(d + (uint32_t)offsetof(Pair<TV>, val),
+                                       p.val + base + off + 32 + lane, pol);
+        cp_async_hint<8>(dm, sd.perm + base + off + 32 + lane, pol);
+      } else {
+        cp_async<4>(d, p.remap + base + off + 32 + lane);
+        cp_async<(int)sizeof(TV)>(d + (uint32_t)offsetof(Pair<TV>, val),
+                                  p.val + base + off + 32 + lane);
+        cp_async<8>(dm, sd.perm + base + off + 32 + lane);
+      }
     }
     cp_async_commit();
     const int n = min(32, total - off);

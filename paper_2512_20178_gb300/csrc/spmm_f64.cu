@@ -16,12 +16,4 @@ shiro_status spmm_fused_f64(const shiro_plan_s* P, const void* B, int64_t ldb, i
                                       fused);
 }
 
-shiro_status spmm_bwd_f64(const shiro_plan_s* PT, const void* dC, int64_t lddc, int32_t N,
-                          shiro_dtype dt, void* dCpack, int64_t lddp, void* dB, int64_t lddb,
-                          const void* B, int64_t ldb, void* dA, void* scratch, cudaStream_t s,
-                          bool* done) {
-  return spmm_bwd_typed<double, double>(PT, dC, lddc, N, dt, dCpack, lddp, dB, lddb, B, ldb, dA,
-                                    scratch, s, done);
-}
-
 }  // namespace shiro

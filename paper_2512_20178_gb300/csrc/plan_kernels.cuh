@@ -274,6 +274,14 @@ constexpr int kRadixThreads = 256;
 constexpr int kRadixRounds = 8;
 constexpr int64_t kRadixTile = (int64_t)kRadixThreads * kRadixRounds;  // 2048
 
+// Column of the first nonzero of each chunk item (schedule ordering).
+__global__ void k_chunk_first_col(const Item* __restrict__ items, int64_t n,
+                                  const int32_t* __restrict__ col, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = col[items[i].e0];
+}
+
 __global__ void k_row_ids(const int64_t* __restrict__ rowptr, int64_t M, int32_t* rowid) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);

@@ -356,7 +356,15 @@ shiro_status shiro_sddmm(shiro_plan_t plan, const void* dC, int64_t lddc, const 
 /* Backward of C = A B: dB = A^T dC through the TRANSPOSE plan planT (pack dC by planT into
  * dCpack, then SpMM over it, as shiro_pack_spmm) and dA by shiro_sddmm on `plan`.  dB and dA may be NULL to skip
  * them; dCpack (planT's packed_rows x N, leading dimension lddp) is needed when dB is wanted.
- * scratch must hold shiro_spmm_scratch(planT, N, dt). */
+ * scratch must hold shiro_spmm_scratch(planT, N, dt).
+ * When both are wanted, B is given (device, K x N, 16-byte aligned rows), the rows are 512 bytes
+ * (F32 N = 128 or BF16 N = 256, F32 values) and planT's schedule is pipeline 0 or 6, not
+ * persistent, all of it is one launch over planT: a row j of A^T gathers the dC rows of column j's
+ * nonzeros for dB, and each gathered row's dot product with B[j, :] is that nonzero's dA (one pass
+ * of row gathers instead of two).  dCpack and dB are then bit-identical to the two calls; dA is
+ * summed in another fixed order than shiro_sddmm (per lane, then a tree over the warp), within the
+ * same error bound.  Otherwise the two calls are made.  Calls on plan or planT must not overlap on
+ * the GPU. */
 shiro_status shiro_spmm_backward(shiro_plan_t plan, shiro_plan_t planT, const void* dC,
                                  int64_t lddc, const void* Bpack, int64_t ldp, const void* B,
                                  int64_t ldb, int32_t N, shiro_dtype dt, void* dCpack,

@@ -851,11 +851,33 @@ def form_precision(dev, stream, peak, reps, scale=22, deg=32, N=256, seed=3):
     stp = frac_entry(spb + pack_bytes(R, N, 2), st_ms, peak)
     stp["kernel"] = "k_spmm_lean_fused" if fused_step(N, 2) else "pack + " + spmm_kernel(N, 2)
     stp["traffic"] = traffic_from_profile("k_spmm_lean_fused", wname) if fused_step(N, 2) else None
+    # The backward with dC stored in BF16 too: dB and dA in one launch over the transposed plan,
+    # and the two calls beside it.
+    PT = shiro.Plan.create(rp, col, val, A.M, A.K, 4, 4, flags=shiro.SHIRO_PLAN_TRANSPOSE)
+    RT = PT.info.packed_rows
+    G = torch.randn((A.M, N), device=dev,
+                    generator=torch.Generator(device=dev).manual_seed(seed)).to(torch.bfloat16)
+    Gp = torch.empty((RT, N), dtype=torch.bfloat16, device=dev)
+    dB = torch.empty((A.K, N), dtype=torch.float32, device=dev)
+    dA = torch.empty(A.nnz, dtype=torch.float32, device=dev)
+    sT = PT.new_scratch(N, torch.bfloat16)
+    bwd_ms = timed(lambda: shiro.spmm_backward(P, PT, G, Bp, B=Bd, scratch=sT, dCpack=Gp, dB=dB,
+                                               dA=dA), stream, reps)
+    two_ms = timed(lambda: (PT.pack_spmm(G, Bpack=Gp, out=dB, scratch=sT),
+                            P.sddmm(G, Bp, B=Bd, out=dA)), stream, reps)
+    nzc = int(np.count_nonzero(np.bincount(A.col, minlength=A.K)))
+    one = frac_entry(bwd_bytes(A.K, A.nnz, RT, N, 2, nzc), bwd_ms, peak)
+    one["kernel"] = "k_spmm_lean_bwd"
+    one["traffic"] = traffic_from_profile("k_spmm_lean_bwd", wname)
+    del PT, G, Gp, dB, dA, sT
     return {"workload": wname, "seed": seed, "M": A.M, "nnz": A.nnz, "packed_rows": R,
             "plan_ms": plan_ms, "spmm": e, "pack": frac_entry(pack_bytes(R, N, 2), pk_ms, peak),
             "step": stp, "step_ms": st_ms, "step_GBps_spmm_bytes": gbps(spb, st_ms),
             "gather_bytes": A.nnz * N * 2, "gather_GBps": gbps(A.nnz * N * 2, sp_ms),
-            "gflops": 2.0 * A.nnz * N / (st_ms * 1e-3) / 1e9}
+            "gflops": 2.0 * A.nnz * N / (st_ms * 1e-3) / 1e9,
+            "backward": {"bwd_one_launch": one, "two_calls_ms": two_ms,
+                         "fwd_bwd_ms": st_ms + bwd_ms, "transpose_packed_rows": RT,
+                         "what": "dC stored in BF16 (FP32 accumulation, FP32 dB and dA)"}}
 
 
 def form_gcn(dev, stream, peak, reps, scale=20, deg=16, N=128, F=256, seed=4, tiles=4):

@@ -156,3 +156,46 @@ def test_backward_one_launch_full_size_rmat20():
     es = (synth.uniform_f64(312, synth.STREAM_PERM, 0, 200000) * A.nnz).astype(np.int64)
     eA = gu.sampled_sddmm_error(A, G, B, dA.cpu().numpy(), es)
     assert eA <= gu.TOL, f"dA (sampled) scaled error {eA}"
+
+
+def test_backward_one_launch_full_size_precision_bf16():
+    """The precision workload at full size (R-MAT 2^22, average degree 32, B and dC 2^22 x 256
+    stored in BF16, 4x4 tiles): dB bit-equal to the two calls; dB on sampled rows (random and the
+    64 densest columns of A) and dA on 200,000 sampled nonzeros within the bound of the FP64
+    oracle on the BF16-rounded operands."""
+    shiro = gu.lib()
+    A = synth.rmat(22, 32, 3)
+    N = 256
+    bB = synth.to_bf16_bits(synth.dense_normal(A.K, N, 3))
+    bG = synth.to_bf16_bits(synth.dense_normal(A.M, N, 313))
+    d = gu.dev()
+    P = gu.plan_of(A, 4, 4)
+    PT = gu.plan_of(A, 4, 4, shiro.SHIRO_PLAN_TRANSPOSE)
+    Bd = torch.from_numpy(bB.view(np.int16)).to(d).view(torch.bfloat16)
+    Gd = torch.from_numpy(bG.view(np.int16)).to(d).view(torch.bfloat16)
+    Bp = P.pack(Bd)
+    dB_ref = PT.pack_spmm(Gd)
+    dB, dA = shiro.spmm_backward(P, PT, Gd, Bp, B=Bd)
+    torch.cuda.synchronize()
+    P.check()
+    PT.check()
+    assert torch.equal(dB, dB_ref)
+    del dB_ref, Bp
+
+    class _Rows:  # BF16-rounded rows on demand (FP32 copies of both would be 8 GB more)
+        def __init__(self, bits):
+            self.bits, self.shape = bits, bits.shape
+        def __getitem__(self, ix):
+            return synth.bf16_bits_to_f32(self.bits[ix]).reshape(len(ix), -1)
+
+    rpT, colT, perm = oracle.transpose(A)
+    AT = synth.CSR(A.K, A.M, rpT, colT, A.val[perm])
+    degT = np.diff(rpT)
+    rows = np.unique(np.concatenate([
+        (synth.uniform_f64(314, synth.STREAM_PERM, 0, 1000) * A.K).astype(np.int64),
+        np.argsort(degT)[-64:]]))
+    eB = gu.sampled_rows_error(AT, _Rows(bG), dB[torch.from_numpy(rows).to(d)].cpu().numpy(), rows)
+    assert eB.max() <= gu.TOL, f"dB (sampled rows) scaled error {eB.max()}"
+    es = (synth.uniform_f64(315, synth.STREAM_PERM, 0, 200000) * A.nnz).astype(np.int64)
+    eA = gu.sampled_sddmm_error(A, _Rows(bG), _Rows(bB), dA.cpu().numpy(), es)
+    assert eA <= gu.TOL, f"dA (sampled) scaled error {eA}"

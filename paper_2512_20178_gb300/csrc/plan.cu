@@ -525,7 +525,7 @@ static shiro_status transpose_into(shiro_plan_s* P, const Shape& sh, const shiro
 // over the resident warp slots (40 per SM for the 48-register gathers).
 constexpr int64_t kAutoGroupNnz = 256;
 #ifndef SHIRO_CHUNK_TILE_ORDER
-#define SHIRO_CHUNK_TILE_ORDER 1
+#define SHIRO_CHUNK_TILE_ORDER 2
 #endif
 constexpr int64_t kAutoWarpsPerSm = 40;
 
@@ -553,13 +553,16 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
     }
   }
   const int64_t n_chunk_items = (int64_t)items.size();
-  // Chunk items by (row block, column tile of the chunk's first nonzero), row order within: the
-  // chunks in flight at one time then gather from one or two tiles' packed rows, a set that fits
-  // in L2, instead of from their row block's whole packed set.  A long row's partial sums are added
-  // in slot order whatever order its chunks run in, so C does not change.  Measured (ms, row order
-  // -> tile order): R-MAT 2^20 FP32 N = 128 SpMM 0.551 -> 0.545, pack + SpMM 0.745 -> 0.738,
-  // backward 1.128 -> 1.105; N = 64 SpMM 0.364 -> 0.360; R-MAT 2^22 degree 32 BF16 N = 256 SpMM
-  // 5.75 -> 5.63, pack + SpMM 6.70 -> 6.60.
+  // Chunk items by row block, then by the column of the chunk's first nonzero (rows in order for
+  // equal columns).  The chunks in flight at one time then sweep their row block's packed rows in
+  // column order: a hub row's chunk covers a narrow column range, so the rows they gather form a
+  // window of the packed set that stays in L2, instead of the row block's whole packed set.  A long
+  // row's partial sums are added in slot order whatever order its chunks run in, so C does not
+  // change.  Measured (ms; row order -> tile of the first nonzero -> its column): R-MAT 2^20
+  // FP32 N = 128 SpMM 0.551 -> 0.545 -> 0.541, pack + SpMM 0.745 -> 0.739 -> 0.737, backward
+  // 1.128 -> 1.105 -> 1.099; N = 64 SpMM 0.364 -> 0.360 -> 0.359; R-MAT 2^22 degree 32 BF16
+  // N = 256 SpMM 5.75 -> 5.55 -> 5.30, pack + SpMM 6.70 -> 6.60 -> 6.55.
+  // SHIRO_CHUNK_TILE_ORDER: 0 row order, 1 tile order, 2 column order.
   if (SHIRO_CHUNK_TILE_ORDER && n_chunk_items > 1 && P->geo.Pc > 1 &&
       !(P->flags & SHIRO_PLAN_DIAG_ONLY) && n_chunk_items <= P->fseq_cap) {
     std::vector<int32_t> c0((size_t)n_chunk_items);
@@ -578,7 +581,8 @@ shiro_status build_schedule(shiro_plan_s* P, const shiro_opts& o, cudaStream_t s
                         P->rb.begin() - 1;
       const int64_t q = std::upper_bound(P->cb.begin(), P->cb.end(), (int64_t)c0[k]) -
                         P->cb.begin() - 1;
-      key[k] = p * (int64_t)(P->geo.Pc + 1) + q;
+      key[k] = SHIRO_CHUNK_TILE_ORDER == 2 ? p * (P->K + 1) + c0[k]
+                                           : p * (int64_t)(P->geo.Pc + 1) + q;
     }
     std::vector<int64_t> ord((size_t)n_chunk_items);
     for (int64_t k = 0; k < n_chunk_items; ++k) ord[k] = k;

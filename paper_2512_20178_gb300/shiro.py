@@ -438,10 +438,12 @@ def spmm_backward(plan: Plan, planT: Plan, dC, Bpack, B=None, want_dB=True, want
         scratch = planT.new_scratch(N, dC.dtype)
     sb = scratch.numel() if scratch is not None else 0
     ldb = B.stride(0) if B is not None else N
+    lddp = dCpack.stride(0) if dCpack is not None and dCpack.dim() == 2 else N
+    lddb = dB.stride(0) if dB is not None else N
     shiro_spmm_backward(plan.handle, planT.handle if planT is not None else None, _ptr(dC),
                         dC.stride(0), _ptr(Bpack), Bpack.stride(0) if Bpack.dim() == 2 else N,
-                        _ptr(B), ldb, N, dtype_code(dC.dtype), _ptr(dCpack), N, _ptr(dB),
-                        N, _ptr(dA), _ptr(scratch), sb, _stream(stream))
+                        _ptr(B), ldb, N, dtype_code(dC.dtype), _ptr(dCpack), lddp, _ptr(dB),
+                        lddb, _ptr(dA), _ptr(scratch), sb, _stream(stream))
     return dB, dA
 
 

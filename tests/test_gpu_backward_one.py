@@ -199,3 +199,26 @@ def test_backward_one_launch_full_size_precision_bf16():
     es = (synth.uniform_f64(315, synth.STREAM_PERM, 0, 200000) * A.nnz).astype(np.int64)
     eA = gu.sampled_sddmm_error(A, _Rows(bG), _Rows(bB), dA.cpu().numpy(), es)
     assert eA <= gu.TOL, f"dA (sampled) scaled error {eA}"
+
+
+def test_backward_one_launch_strided_outputs():
+    """dB and the packed dC rows written into views with leading dimensions larger than N: the
+    same values as into contiguous buffers, and the padding columns untouched."""
+    shiro = gu.lib()
+    A = synth.rmat(12, 8, 316)
+    N, pad = 128, 16
+    P = gu.plan_of(A, 2, 2)
+    PT = gu.plan_of(A, 2, 2, shiro.SHIRO_PLAN_TRANSPOSE)
+    d = gu.dev()
+    Bd = torch.from_numpy(synth.dense_normal(A.K, N, 317)).to(d)
+    Gd = torch.from_numpy(synth.dense_normal(A.M, N, 318)).to(d)
+    Bp = P.pack(Bd)
+    dB0, dA0 = shiro.spmm_backward(P, PT, Gd, Bp, B=Bd)
+    Gpw = torch.full((PT.info.packed_rows, N + pad), 7.0, device=d)
+    dBw = torch.full((A.K, N + pad), 7.0, device=d)
+    dA = torch.empty(A.nnz, device=d)
+    shiro.spmm_backward(P, PT, Gd, Bp, B=Bd, dCpack=Gpw[:, :N], dB=dBw[:, :N], dA=dA)
+    torch.cuda.synchronize()
+    assert torch.equal(dBw[:, :N], dB0) and torch.equal(dA, dA0)
+    assert torch.equal(Gpw[:, :N], PT.pack(Gd))
+    assert bool((dBw[:, N:] == 7.0).all()) and bool((Gpw[:, N:] == 7.0).all())

@@ -58,8 +58,9 @@ FORMS = ("backward", "bf16", "nsweep", "autotune", "cusparse", "precision", "gcn
 
 def fused_step(N, sz):
     """Whether shiro_pack_spmm runs as one launch (k_spmm_lean_fused) with the default schedule:
-    rows of 512 bytes (FP32 N = 128, BF16 N = 256)."""
-    return N * sz == 512
+    FP32 rows of 512 bytes (N = 128).  BF16 rows of 512 bytes take the pack and then the TMA
+    gather4 ring, two launches."""
+    return N * sz == 512 and sz == 4
 
 
 def spmm_kernel(N, sz):

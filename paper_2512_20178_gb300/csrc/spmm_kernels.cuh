@@ -891,6 +891,12 @@ static shiro_status spmm_fused_typed(const shiro_plan_s* P, const void* B, int64
     // 0.509, BF16 N = 128 0.560 -> 0.565) and take the two launches.
     const int row = N * (int)esz;
     if (row != 512) return SHIRO_OK;
+    // BF16 rows of 512 bytes with the automatic pipeline: the pack, then the TMA gather4 ring
+    // (pipeline 7), are faster as two launches than this one with register gathers (R-MAT 2^22
+    // avg degree 32, N = 256, chunks in column order: 0.98 + 5.29 ms against 6.55 ms).
+    if constexpr (!std::is_same<TB, float>::value) {
+      if (P->opts.pipeline == 0 && v.vec == 8 && g4_ok<TV, TB, 8>(P, prm)) return SHIRO_OK;
+    }
     *fused = true;
     if constexpr (std::is_same<TB, float>::value) {
       if (v.vec == 4) return launch_lean_fused<TV, TB, 4, 1>(P, prm, f, s);

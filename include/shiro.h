@@ -105,7 +105,7 @@ typedef struct {
                                FP32/BF16 rows of 128 to 512 bytes (in its counter form except
                                for BF16 rows of 256 bytes; 5 in persistent mode), 4 for FP32/BF16
                                rows of 1-2 KB, else 5 (the fastest measured for each row size;
-                               shiro_pack_spmm runs rows of 512 bytes as one fused launch);
+                               shiro_pack_spmm runs FP32 rows of 512 bytes as one fused launch);
                             1: staged through shared memory by per-lane asynchronous copies, two
                                stages per warp;
                             2: staged by one TMA bulk copy per row, two stages per warp (rows of
@@ -302,9 +302,11 @@ shiro_status shiro_spmm(shiro_plan_t plan, const void* Bpack, int64_t ldp, const
 
 /* Pack + SpMM in one call (Sec. 5.1 stages 3 and 5 overlapped): the same results as shiro_pack
  * (Bpack[r] = B[pack_src[r]], bit-exact) followed by shiro_spmm(plan, Bpack, ldp, B, ldb, ...)
- * (C bit-identical: the same work items summed in the same order).  For FP32 or BF16 rows of 512
- * bytes (N = 128 / 256) with pipeline 0 or 6, not persistent, and B, Bpack and C aligned to 16
- * bytes, it is one launch: the plan orders the pack of row block p + 1
+ * (C bit-identical: the same work items summed in the same order).  For FP32 rows of 512 bytes
+ * (N = 128) with pipeline 0 or 6, and BF16 rows of 512 bytes (N = 256) with pipeline 6, not
+ * persistent, and B, Bpack and C aligned to 16 bytes, it is one launch (BF16 rows of 512 bytes
+ * with pipeline 0 take the pack and then the TMA gather4 ring, measured faster): the plan orders
+ * the pack of row block p + 1
  * among the SpMM work of block p (after the pack of block 0), and a warp starts an item of block p
  * once every packed row of block p is written (a per-block count in the plan; the wait is bounded
  * and sets a device status bit that shiro_plan_check reports if it runs out).  Otherwise it

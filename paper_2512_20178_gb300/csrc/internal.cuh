@@ -183,7 +183,8 @@ template <typename K>
 inline cudaError_t blocks_per_sm(int* per_sm, K kern, int threads, size_t smem) {
   return occupancy_cached(per_sm, reinterpret_cast<const void*>(kern), threads, smem);
 }
-// Pack + SpMM (one launch for 512-byte rows, else pack then SpMM); same results as the two.
+// Pack + SpMM (one launch for FP32 rows of 512 bytes, and BF16 ones with pipeline 6; else pack
+// then SpMM); same results as the two.
 shiro_status launch_pack_spmm(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N,
                               shiro_dtype dt, void* Bpack, int64_t ldp, void* C, int64_t ldc,
                               uint32_t flags, void* scratch, size_t scratch_bytes, cudaStream_t s);

@@ -857,8 +857,8 @@ static shiro_status launch_lean_fused(const shiro_plan_s* P, const SpmmParams<TV
 }
 
 // Pack + SpMM in one launch (k_spmm_lean_fused): FP32 / BF16 rows of 512 bytes in one fragment per
-// lane, pipeline 0 or 6, not persistent, operands aligned to the fragment.  *fused = false (nothing
-// launched) otherwise.
+// lane, pipeline 0 or 6 (BF16 with pipeline 0 only where the gather4 ring cannot run), not
+// persistent, operands aligned to the fragment.  *fused = false (nothing launched) otherwise.
 template <typename TV, typename TB>
 static shiro_status spmm_fused_typed(const shiro_plan_s* P, const void* B, int64_t ldb, int32_t N,
                                      shiro_dtype dt, void* Bpack, int64_t ldp, void* C,
@@ -932,8 +932,8 @@ static shiro_status launch_lean_bwd(const shiro_plan_s* P, const SpmmParams<TV, 
 
 // The backward in one launch (k_spmm_lean_bwd) on the TRANSPOSE plan PT: dCpack and dB as
 // spmm_fused_typed(PT, dC, ...) computes them, plus dA (A's nonzero order) from the same gathers
-// and B.  For the shapes and schedules spmm_fused_typed runs in one launch, with B aligned to 16
-// bytes; *done = false (nothing launched) otherwise.
+// and B.  For FP32 / BF16 rows of 512 bytes with pipeline 0 or 6, not persistent, operands and B
+// aligned to 16 bytes; *done = false (nothing launched) otherwise.
 template <typename TV, typename TB>
 static shiro_status spmm_bwd_typed(const shiro_plan_s* PT, const void* dC, int64_t lddc,
                                    int32_t N, shiro_dtype dt, void* dCpack, int64_t lddp,

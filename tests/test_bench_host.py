@@ -1,5 +1,5 @@
 """Host-side reporting logic of bench.py (CPU only): clock-sample parsing, the kernel name the
-roofline reports, and the rule that a stored DRAM-traffic figure is used only while the kernel
+roofline reports, the step's launch form and the backward's byte count, and the rule that a stored DRAM-traffic figure is used only while the kernel
 sources it was measured on are unchanged."""
 import json
 import os
@@ -35,6 +35,20 @@ def test_spmm_kernel_names():
     assert bench.spmm_kernel(256, 2) == "k_spmm_g4"          # BF16 512-byte rows: TMA gather4
     assert bench.spmm_kernel(256, 4) == "k_spmm_lring"       # 1 KB rows
     assert bench.spmm_kernel(16, 4) == "k_spmm"
+
+
+def test_step_kernel_and_backward_bytes():
+    # shiro_pack_spmm is one launch for FP32 rows of 512 bytes; BF16 rows of 512 bytes take the
+    # pack and then the gather4 ring.
+    assert bench.fused_step(128, 4) and not bench.fused_step(256, 2)
+    assert not bench.fused_step(64, 4) and not bench.fused_step(256, 4)
+    # The one-launch backward counts the pack of dC, the SpMM of A^T, one B row per non-empty row
+    # of A^T and the dA values, each once (R-MAT 2^20 degree 16, N = 128, FP32: 2,970,272,864).
+    K, nnz, RT, N, nzc = 1 << 20, 16086807, 1267409, 128, 547191
+    assert bench.bwd_bytes(K, nnz, RT, N, 4, nzc) == 2970272864
+    assert bench.bwd_bytes(K, nnz, RT, N, 4, nzc) == (bench.pack_bytes(RT, N, 4) +
+                                                      bench.spmm_bytes(K, nnz, RT, N, 4) +
+                                                      nzc * N * 4 + nnz * 4)
 
 
 def test_traffic_record_follows_the_sources(tmp_path, monkeypatch):

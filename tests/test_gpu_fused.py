@@ -1,4 +1,6 @@
-"""shiro_pack_spmm: pack + SpMM in one call (one launch for rows of 512 bytes).
+"""shiro_pack_spmm: pack + SpMM in one call (one launch for FP32 rows of 512 bytes, and for BF16
+ones with pipeline 6; BF16 rows of 512 bytes with the automatic pipeline take the pack and the
+gather4 ring).
 
 Bpack must equal shiro_pack's bit for bit and C must equal shiro_spmm's over those rows bit for bit
 (the same work items, summed in the same order), on every row shape, on 1D plans with local

@@ -731,9 +731,26 @@ def measure_forms(args, fset, A, B, P, Bd, Bp, C, scratch, rp, col, val, dev, st
         one["traffic"] = traffic_from_profile("k_spmm_lean_bwd", wname)
         one["bytes_definition"] = ("pack 2*RT*N*4 + RT*4, SpMM of A^T (K+1)*8 + nnz*8 + RT*N*4 + "
                                    "K*N*4, B rows nzc*N*4, dA nnz*4")
+        # Rows of 256 bytes (N = 64): the one launch against the two calls.
+        narrow = {}
+        for n in (64,):
+            Bn = torch.from_numpy(synth.dense_normal(A.K, n, 12)).to(dev)
+            Gn = torch.randn((A.M, n), device=dev, generator=torch.Generator(device=dev).manual_seed(6))
+            Bpn = P.pack(Bn)
+            Gpn = torch.empty((RT, n), dtype=torch.float32, device=dev)
+            dBn = torch.empty((A.K, n), dtype=torch.float32, device=dev)
+            sTn = PT.new_scratch(n, torch.float32)
+            one_n = run(lambda: shiro.spmm_backward(P, PT, Gn, Bpn, B=Bn, scratch=sTn, dCpack=Gpn,
+                                                    dB=dBn, dA=dA))
+            two_n = run(lambda: (PT.pack_spmm(Gn, Bpack=Gpn, out=dBn, scratch=sTn),
+                                 P.sddmm(Gn, Bpn, out=dA)))
+            narrow[str(n)] = {"one_launch": frac_entry(bwd_bytes(A.K, A.nnz, RT, n, 4, nzc), one_n,
+                                                       peak),
+                              "two_calls_ms": two_n}
+            del Bn, Gn, Bpn, Gpn, dBn, sTn
         out["backward"] = {
             "workload": wname, "fwd_ms": fwd_ms, "fwd_bwd_ms": fwd_ms + bwd_ms,
-            "bwd_one_launch": one,
+            "bwd_one_launch": one, "narrow_rows_fp32": narrow,
             "two_calls": {"fwd_bwd_ms": fwd_ms + db_ms + da_ms, "bwd_ms": db_ms + da_ms,
                           "what": "shiro_pack_spmm on the transposed plan, then shiro_sddmm"},
             "dB_step_ms": db_ms, "dB_spmm": frac_entry(spmm_bytes(A.K, A.nnz, RT, N, 4), db_spmm, peak),

@@ -359,8 +359,9 @@ shiro_status shiro_sddmm(shiro_plan_t plan, const void* dC, int64_t lddc, const 
  * dCpack, then SpMM over it, as shiro_pack_spmm) and dA by shiro_sddmm on `plan`.  dB and dA may be NULL to skip
  * them; dCpack (planT's packed_rows x N, leading dimension lddp) is needed when dB is wanted.
  * scratch must hold shiro_spmm_scratch(planT, N, dt).
- * When both are wanted, B is given (device, K x N, 16-byte aligned rows), the rows are 512 bytes
- * (F32 N = 128 or BF16 N = 256, F32 values) and planT's schedule is pipeline 0 or 6, not
+ * When both are wanted, B is given (device, K x N, rows aligned to 16 bytes for rows of 512 bytes,
+ * to 8 for rows of 256), the rows are 256 or 512 bytes (F32 N = 64 / 128 or BF16 N = 128 / 256,
+ * F32 values) and planT's schedule is pipeline 0 or 6, not
  * persistent, all of it is one launch over planT: a row j of A^T gathers the dC rows of column j's
  * nonzeros for dB, and each gathered row's dot product with B[j, :] is that nonzero's dA (one pass
  * of row gathers instead of two).  dCpack and dB are then bit-identical to the two calls; dA is

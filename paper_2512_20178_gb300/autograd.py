@@ -2,8 +2,8 @@
 
 Forward: pack B's rows named by every tile's Cols and SpMM over the packed rows (one library
 call, shiro_pack_spmm).  Backward: dB = A^T dC through the TRANSPOSE plan (pack dC, SpMM) and
-dA = SDDMM(dC, B) on A's pattern, in one library call (shiro_spmm_backward); for rows of 512
-bytes both come from one launch that gathers each dC row once.  All of it runs in the CUDA
+dA = SDDMM(dC, B) on A's pattern, in one library call (shiro_spmm_backward); for rows of 256 or
+512 bytes both come from one launch that gathers each dC row once.  All of it runs in the CUDA
 library.
 """
 from __future__ import annotations

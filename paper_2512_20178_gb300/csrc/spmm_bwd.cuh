@@ -1,4 +1,5 @@
-// spmm_bwd.cuh -- the backward of C = A B in one launch over the TRANSPOSE plan of A:
+// spmm_bwd.cuh -- the backward of C = A B in one launch over the TRANSPOSE plan of A (rows of 256
+// or 512 bytes):
 //   * the pack of dC's rows named by the plan (dCpack[r] = dC[pack_src[r]], Sec. 5.1 stage 3);
 //   * dB = A^T dC over the packed rows (the transposed SpMM, Sec. 5.1 stage 5);
 //   * dA on A's pattern, dA[e] = <dC[row e, :], B[col e, :]>, from the same gathered dC rows.
@@ -56,23 +57,29 @@ __device__ __forceinline__ void cp_async_hint(uint32_t smem, const void* gmem, u
                : "memory");
 }
 
-// The lane's 16-byte slice of a B row as floats.  B's rows are read once per row of A^T (a long
-// row's chunks read it again, mostly from L2); with SHIRO_BWD_HINT the read carries an
+// The lane's 16- or 8-byte slice of a B row as floats.  B's rows are read once per row of A^T (a
+// long row's chunks read it again, mostly from L2); with SHIRO_BWD_HINT the read carries an
 // evict-first L2 policy so that it displaces fewer of the gathered dC rows.
 template <typename TB, int VEC>
 __device__ __forceinline__ void load_b_row(const TB* p, float (&f)[VEC]) {
-  static_assert(VEC * sizeof(TB) == 16, "16-byte slices");
+  constexpr int WORDS = VEC * (int)sizeof(TB) / 4;
+  static_assert(WORDS == 4 || WORDS == 2, "16- or 8-byte slices");
   if constexpr (SHIRO_BWD_HINT) {
-    uint32_t w[4];
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;\n"
-                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
-                 : "l"(p), "l"(evict_first_policy()));
+    uint32_t w[WORDS];
+    if constexpr (WORDS == 4)
+      asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;\n"
+                   : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                   : "l"(p), "l"(evict_first_policy()));
+    else
+      asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;\n"
+                   : "=r"(w[0]), "=r"(w[1])
+                   : "l"(p), "l"(evict_first_policy()));
     if constexpr (std::is_same<TB, float>::value) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) f[v] = __uint_as_float(w[v]);
+      for (int v = 0; v < WORDS; ++v) f[v] = __uint_as_float(w[v]);
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < WORDS; ++k) {
         f[2 * k] = bf16_lo(w[k]);
         f[2 * k + 1] = bf16_hi(w[k]);
       }

@@ -932,8 +932,8 @@ static shiro_status launch_lean_bwd(const shiro_plan_s* P, const SpmmParams<TV, 
 
 // The backward in one launch (k_spmm_lean_bwd) on the TRANSPOSE plan PT: dCpack and dB as
 // spmm_fused_typed(PT, dC, ...) computes them, plus dA (A's nonzero order) from the same gathers
-// and B.  For FP32 / BF16 rows of 512 bytes with pipeline 0 or 6, not persistent, operands and B
-// aligned to 16 bytes; *done = false (nothing launched) otherwise.
+// and B.  For FP32 / BF16 rows of 256 or 512 bytes with pipeline 0 or 6, not persistent, operands
+// and B aligned to the lane's 8- or 16-byte slice; *done = false (nothing launched) otherwise.
 template <typename TV, typename TB>
 static shiro_status spmm_bwd_typed(const shiro_plan_s* PT, const void* dC, int64_t lddc,
                                    int32_t N, shiro_dtype dt, void* dCpack, int64_t lddp,
@@ -947,10 +947,11 @@ static shiro_status spmm_bwd_typed(const shiro_plan_s* PT, const void* dC, int64
     if (PT->opts.persistent || (PT->opts.pipeline != 0 && PT->opts.pipeline != 6)) return SHIRO_OK;
     if (PT->n_fseq > INT32_MAX || !PT->d_perm) return SHIRO_OK;
     const size_t esz = dtype_size(dt);
-    if ((int64_t)N * (int64_t)esz != 512) return SHIRO_OK;
-    const int v16 = (int)(16 / esz);
-    if (!(aligned(dCpack, lddp, esz, v16) && aligned(dB, lddb, sizeof(TA), v16) &&
-          aligned(dC, lddc, esz, v16) && aligned(B, ldb, esz, v16)))
+    const int64_t row = (int64_t)N * (int64_t)esz;
+    if (row != 512 && row != 256) return SHIRO_OK;
+    const int vec = (int)(row / 32 / (int64_t)esz);  // a 16- or 8-byte slice per lane
+    if (!(aligned(dCpack, lddp, esz, vec) && aligned(dB, lddb, sizeof(TA), vec) &&
+          aligned(dC, lddc, esz, vec) && aligned(B, ldb, esz, vec)))
       return SHIRO_OK;
     const SpmmParams<TV, TB> prm =
         make_params<TV, TB>(PT, dCpack, lddp, dC, lddc, N, dt, dB, lddb, 0, scratch);
@@ -959,9 +960,11 @@ static shiro_status spmm_bwd_typed(const shiro_plan_s* PT, const void* dC, int64
     SdParams<TB> sd{(const TB*)B, (uint32_t)ldb, (float*)dA, PT->d_perm};
     *done = true;
     if constexpr (std::is_same<TB, float>::value)
-      return launch_lean_bwd<TV, TB, 4>(PT, prm, f, sd, s);
+      return row == 512 ? launch_lean_bwd<TV, TB, 4>(PT, prm, f, sd, s)
+                        : launch_lean_bwd<TV, TB, 2>(PT, prm, f, sd, s);
     else
-      return launch_lean_bwd<TV, TB, 8>(PT, prm, f, sd, s);
+      return row == 512 ? launch_lean_bwd<TV, TB, 8>(PT, prm, f, sd, s)
+                        : launch_lean_bwd<TV, TB, 4>(PT, prm, f, sd, s);
   }
 }
 

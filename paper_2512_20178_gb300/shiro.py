@@ -420,7 +420,7 @@ class Plan:
 def spmm_backward(plan: Plan, planT: Plan, dC, Bpack, B=None, want_dB=True, want_dA=True,
                   scratch=None, stream=None, dCpack=None, dB=None, dA=None):
     """dB = A^T dC (through planT) and dA on A's pattern, in one C call (one launch for rows of
-    512 bytes when B is given).  dCpack, dB and dA may be passed preallocated."""
+    256 or 512 bytes when B is given).  dCpack, dB and dA may be passed preallocated."""
     N = dC.shape[1]
     dev = dC.device
     acc = _ACC[dC.dtype]

@@ -1,11 +1,11 @@
 """shiro_spmm_backward in one launch: the pack of dC's rows, dB = A^T dC and dA on A's pattern
-computed from the same gathered dC rows, for rows of 512 bytes (FP32 N = 128, BF16 N = 256) when
-the caller passes B.
+computed from the same gathered dC rows, for rows of 256 or 512 bytes (FP32 N = 64 / 128, BF16
+N = 128 / 256) when the caller passes B.
 
 dB and the packed dC rows must equal the two-call path (shiro_pack_spmm on the TRANSPOSE plan) bit
 for bit: the same work items summed in the same order.  dA is summed in another order than the
 SDDMM kernels (per lane, then a tree over the warp), so it is held to the scaled tolerance of the
-FP64 oracle, on every nonzero.  Cases: both row shapes, hub rows cut into chunks, 1D plans whose
+FP64 oracle, on every nonzero.  Cases: the four row shapes, hub rows cut into chunks, 1D plans whose
 local diagonal tiles read dC in place, empty rows and columns, a ragged grid, more row blocks than
 rows, and every call twice in a row (the per-block counters and the work counter are reset by each
 call)."""
@@ -76,7 +76,8 @@ def _case(A, N, dt, Pr, Pc, flags=0, opts=None, seed=300):
     return P, PT, Bd, Gd, Bp
 
 
-@pytest.mark.parametrize("dt,N", [(torch.float32, 128), (torch.bfloat16, 256)])
+@pytest.mark.parametrize("dt,N", [(torch.float32, 128), (torch.bfloat16, 256), (torch.float32, 64),
+                                  (torch.bfloat16, 128)])
 def test_backward_one_launch_row_shapes(dt, N):
     _case(synth.rmat(13, 12, 301), N, dt, 4, 4)
 
